@@ -1,0 +1,230 @@
+/*
+ * cgh.h -- C ABI of libcgh: point-source Fresnel computer-generated
+ * holograms on one sm_103a GPU.
+ *
+ * The computation (Shimobaba et al., Section 1, Eq. 1):
+ *
+ *     I(x_h, y_h) = sum_{j<N} A_j cos( P_j ((x_h - x_j)^2 + (y_h - y_j)^2) ),
+ *     P_j = pi p^2 / (lambda z_j),
+ *
+ * for every pixel x_h = 0..Nx-1, y_h = 0..Ny-1 (integer pixel indices; the
+ * object coordinates x_j, y_j are in units of the pixel pitch p, as the paper
+ * normalises them).  lambda (wavelength), p (pixel pitch) and z_j (depth) are
+ * in metres.  The hologram is stored row-major: out[y_h * Nx + x_h].
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Pointers marked "device" must be CUDA device (or managed) memory of
+ *    the handle's device; "host" pointers are ordinary process memory.
+ *    The caller owns every buffer it passes; the library never frees them.
+ *  * points: N x 2 floats, interleaved (x_0, y_0, x_1, y_1, ...).
+ *    A, z: N floats.  4-byte alignment suffices for all float arrays.
+ *  * Calls taking a `stream` (a cudaStream_t passed as void*, NULL = the
+ *    legacy default stream) are asynchronous on that stream and never
+ *    synchronise it, unless stated.  One handle must not be used from two
+ *    streams at once: its workspace is shared between calls.
+ *  * Argument errors are detected on the host and returned before any work
+ *    is enqueued; outputs are untouched then.  Values that only the device
+ *    sees (z_j <= 0, non-finite x_j, y_j, A_j, z_j) make the affected point
+ *    contribute nothing and raise a bit in the handle's device status word,
+ *    which cgh_last_device_status() reports.
+ *  * The library never aborts the process, traps the GPU, or waits without
+ *    a bound: every device-side wait gives up after about one second and
+ *    records CGH_ERR_TIMEOUT in the device status word.
+ *  * Workspace (point records, phase/exponential tables, partial sums) is
+ *    owned by the handle, grows on demand with cudaMalloc, and is freed by
+ *    cgh_destroy.  Growth is refused (CGH_ERR_UNSUPPORTED) while the stream
+ *    is being captured into a CUDA graph: run one uncaptured call of the same
+ *    shape first.
+ */
+#ifndef CGH_H
+#define CGH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cgh_ctx *cgh_handle;
+
+typedef enum {
+    CGH_OK = 0,
+    CGH_ERR_INVALID_ARG = 1,  /* rejected argument (host) or bad point (device) */
+    CGH_ERR_CUDA = 2,         /* a CUDA call failed; cgh_last_error() has text   */
+    CGH_ERR_NOMEM = 3,        /* workspace allocation failed                     */
+    CGH_ERR_UNSUPPORTED = 4,  /* valid request this build cannot serve           */
+    CGH_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up              */
+} cgh_status;
+
+typedef enum {
+    /* Direct sum of Eq. 1 in FP32: exact fixed-point phase per image axis
+     * (the separable form of the paper's Eq. 2 recurrence, Section 2.1),
+     * point tiles staged in shared memory by bulk copies (the paper's
+     * shared-memory staging, Section 2.1), hardware cosine (the paper's
+     * "native cos").  max |I - I_ref| <= 1e-4 sum|A_j|. */
+    CGH_DIRECT_FP32 = 0,
+    /* Separable form I = Re(U diag(A) V^T), U[x,j] = exp(i P_j (x - x_j)^2),
+     * V[y,j] = exp(i P_j (y - y_j)^2) (exact because the phase of Eq. 1 is
+     * a sum of an x part and a y part), as a tcgen05 tensor-core GEMM with
+     * FP32 accumulation.  Operands in BF16 / FP16 (single pass, relative RMS
+     * error about 1e-2 / 1e-3) or split hi+lo FP16 (three products,
+     * relative RMS error <= 1e-4). */
+    CGH_SEP_BF16 = 1,
+    CGH_SEP_FP16 = 2,
+    CGH_SEP_FP16X3 = 3,
+    /* One thread per pixel, plain loop over points, 64-bit fixed-point phase
+     * and cospif (the unoptimised kernel of the paper's Fig. 2b, restated).
+     * Slow; for checking. */
+    CGH_NAIVE_FP32 = 4
+} cgh_method;
+
+/* Create a handle bound to CUDA device `device` (made current on the calling
+ * thread).  *out receives the handle.  Errors: CGH_ERR_INVALID_ARG (out NULL,
+ * bad device), CGH_ERR_CUDA. */
+cgh_status cgh_create(cgh_handle *out, int device);
+
+/* Free the handle and its workspace.  Synchronises the device first.
+ * NULL is accepted and ignored. */
+cgh_status cgh_destroy(cgh_handle h);
+
+/* Eq. 1 for one hologram.  points, A, z: device, N points (N >= 0; N = 0
+ * yields zeros).  out: device, Ny*Nx floats, written completely.  lambda, p:
+ * finite and > 0.  1 <= Nx, Ny <= 32768, N <= 2^24.  method: a cgh_method.
+ * Errors: CGH_ERR_INVALID_ARG (NULL pointer, bad size or constant, unknown
+ * method), CGH_ERR_UNSUPPORTED, CGH_ERR_NOMEM, CGH_ERR_CUDA. */
+cgh_status cgh_forward(cgh_handle h, const float *points, const float *A,
+                       const float *z, int N, double lambda, double p,
+                       int Nx, int Ny, float *out, int method, void *stream);
+
+/* cgh_forward from HOST buffers: copies points, A, z to the handle's
+ * workspace, computes, copies the hologram back into out_host (Ny*Nx
+ * floats) and synchronises the stream before returning.  Pinned host
+ * memory gives the fastest copies; pageable memory works too. */
+cgh_status cgh_forward_host(cgh_handle h, const float *points_host,
+                            const float *A_host, const float *z_host, int N,
+                            double lambda, double p, int Nx, int Ny,
+                            float *out_host, int method, void *stream);
+
+/* Adjoint of Eq. 1.  grad_out: device, Ny*Nx floats, dL/dI for some loss L.
+ * Writes (device, N entries each; grad_points N x 2 interleaved):
+ *   grad_A[j]          = sum_pix G cos(phi)
+ *   grad_points[2j]    = 2 P_j A_j sum_pix G sin(phi) (x_h - x_j)
+ *   grad_points[2j+1]  = 2 P_j A_j sum_pix G sin(phi) (y_h - y_j)
+ *   grad_z[j]          = (P_j A_j / z_j) sum_pix G sin(phi) r^2
+ * with phi = P_j r^2, r^2 = (x_h - x_j)^2 + (y_h - y_j)^2 (derivatives of
+ * Eq. 1; dP_j/dz_j = -P_j/z_j).  Any of the three outputs may be NULL to
+ * skip it.  method: CGH_DIRECT_FP32 (FP32, point-owned sums, deterministic)
+ * or CGH_SEP_FP16X3 (two split-FP16 tensor-core GEMMs, G V and G^T U, with
+ * the pixel sums fused into their epilogues).  Errors as cgh_forward. */
+cgh_status cgh_backward(cgh_handle h, const float *points, const float *A,
+                        const float *z, int N, double lambda, double p,
+                        int Nx, int Ny, const float *grad_out,
+                        float *grad_points, float *grad_A, float *grad_z,
+                        int method, void *stream);
+
+/* One problem of a batch; every pointer is device memory (see cgh_forward). */
+typedef struct {
+    const float *points;
+    const float *A;
+    const float *z;
+    int N;
+    double lambda;
+    double p;
+    int Nx;
+    int Ny;
+    float *out;
+} cgh_problem;
+
+/* Many holograms of uneven size, N and wavelength in one persistent launch
+ * (after one prologue launch).  probs: host array of `count` problems
+ * (1 <= count <= 4096).  The work list of (problem, tile) items is built on
+ * the host, sorted longest-first, and pulled by the persistent CTAs from an
+ * atomic counter.  method: CGH_DIRECT_FP32 or CGH_SEP_FP16X3.  The call may
+ * be captured into a CUDA graph once an uncaptured call of the same batch
+ * geometry has sized the workspace.  Errors as cgh_forward. */
+cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int count,
+                     int method, void *stream);
+
+/* Tile shape of the direct kernel. */
+typedef struct {
+    int tile_x;            /* pixels per CTA along x           */
+    int tile_y;            /* pixels per CTA along y           */
+    int vec_x;             /* pixels per thread along x        */
+    int vec_y;             /* pixels per thread along y        */
+    int points_per_stage;  /* points per shared-memory stage   */
+} cgh_direct_tile;
+
+/* Number of direct-kernel tile shapes compiled into this build, and the
+ * i-th of them (0 <= i < count). */
+int cgh_direct_tile_count(void);
+cgh_status cgh_direct_tile_get(int i, cgh_direct_tile *out);
+
+/* Force a tile shape for CGH_DIRECT_FP32 (NULL: back to automatic choice).
+ * Errors: CGH_ERR_UNSUPPORTED if the shape is not compiled in. */
+cgh_status cgh_set_direct_tile(cgh_handle h, const cgh_direct_tile *tile);
+
+/* Autotuner: time every compiled tile shape (CUDA events on `stream`,
+ * synchronising it) for a problem of this size, remember the fastest for
+ * the size bucket, and write it to *chosen (may be NULL).  The choice is
+ * kept in the handle and, if the environment variable CGH_TUNE_CACHE names
+ * a file, appended there as one JSON object per line (device name, size
+ * bucket, tile) and read back by later handles. */
+cgh_status cgh_tune(cgh_handle h, int N, int Nx, int Ny, int method,
+                    void *stream, cgh_direct_tile *chosen);
+
+/* Kernels whose launches the handle can time (cgh_kernel_time). */
+typedef enum {
+    CGH_K_PROLOGUE = 0,       /* per-point records                      */
+    CGH_K_DIRECT_TABLES = 1,  /* per-axis angle tables (direct path)    */
+    CGH_K_DIRECT = 2,         /* direct point loop                      */
+    CGH_K_NAIVE = 3,          /* naive one-thread-per-pixel loop        */
+    CGH_K_SEP_TABLES = 4,     /* U / V exponential tables               */
+    CGH_K_GEMM = 5,           /* tcgen05 GEMM (forward)                 */
+    CGH_K_BWD_DIRECT = 6,     /* direct adjoint point-owned sums        */
+    CGH_K_BWD_GEMM = 7,       /* separable adjoint GEMMs + fused sums   */
+    CGH_K_BWD_REDUCE = 8,     /* adjoint partial-sum reduction          */
+    CGH_K_BATCH = 9,          /* persistent batch kernel                */
+    CGH_K_AUX = 10,           /* small helpers (conversions, fills)     */
+    CGH_K_COUNT = 16
+} cgh_kernel_id;
+
+/* enable != 0: from now on bracket every kernel launch of this handle with
+ * CUDA events recorded on the launch's own stream; enable == 0: stop.  Both
+ * reset the accumulated times. */
+cgh_status cgh_kernel_timing(cgh_handle h, int enable);
+
+/* Total device time (ms, from the events) and number of launches of kernel
+ * `kernel` (a cgh_kernel_id) since timing was enabled.  Synchronises on the
+ * recorded events. */
+cgh_status cgh_kernel_time(cgh_handle h, int kernel, double *total_ms,
+                           uint64_t *launches);
+
+/* Synchronise `stream`, then read and clear the handle's device status
+ * word: CGH_OK, CGH_ERR_INVALID_ARG (a point had z <= 0 or a non-finite
+ * value), CGH_ERR_TIMEOUT (a bounded wait gave up), CGH_ERR_CUDA. */
+cgh_status cgh_last_device_status(cgh_handle h, void *stream);
+
+/* Number of kernels this handle has launched since creation. */
+uint64_t cgh_launch_count(cgh_handle h);
+
+/* Static text for a status code (never NULL). */
+const char *cgh_status_string(int status);
+
+/* Text of the handle's most recent error (never NULL; "" if none). */
+const char *cgh_last_error(cgh_handle h);
+
+/* Diagnostic: D[m*N + n] = sum_k A[m*K + k] * B[n*K + k] on the tcgen05
+ * GEMM used by the separable methods.  A: device, M x K, B: device, N x K,
+ * both 16-bit (is_bf16 = 0: FP16, 1: BF16), K-major; D: device FP32 M x N.
+ * K must be a positive multiple of 64; M, N >= 1. */
+cgh_status cgh_debug_gemm(cgh_handle h, const void *A, const void *B,
+                          float *D, int M, int N, int K, int is_bf16,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGH_H */

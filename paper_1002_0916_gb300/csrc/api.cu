@@ -1,0 +1,448 @@
+// api.cu -- the C ABI of libcgh (include/cgh.h): handles, argument checks,
+// workspace, dispatch to the kernels.  The paper's host steps (Section 2:
+// initialise, allocate, send input, run the kernel, read back, release)
+// map onto cgh_create / cgh_forward(_host) / cgh_destroy.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <unordered_map>
+
+#include "api_internal.h"
+#include "common.cuh"
+
+using namespace cgh;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+// --------------------------------------------------------------- errors
+cgh_status cgh_ctx::fail(cgh_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(err, sizeof(err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+cgh_status cgh_ctx::cuda_fail(cudaError_t e, const char *where) {
+    cudaGetLastError();  // clear a sticky non-fatal error
+    return fail(e == cudaErrorMemoryAllocation ? CGH_ERR_NOMEM : CGH_ERR_CUDA,
+                "%s: %s", where, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ workspace
+cgh_status cgh_ctx::ensure(Buffer &b, size_t bytes, cudaStream_t s,
+                           const char *what) {
+    if (bytes <= b.bytes) return CGH_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+        cs != cudaStreamCaptureStatusNone)
+        return fail(CGH_ERR_UNSUPPORTED,
+                    "%s workspace must grow to %zu bytes during stream capture;"
+                    " run one uncaptured call of this shape first",
+                    what, bytes);
+    if (b.ptr) {
+        cudaError_t e = cudaFree(b.ptr);  // implicit device synchronisation
+        b.ptr = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
+    }
+    size_t want = bytes + bytes / 8;  // some headroom for nearby shapes
+    want = (want + 4095) & ~(size_t)4095;
+    cudaError_t e = cudaMalloc(&b.ptr, want);
+    if (e != cudaSuccess) {
+        b.ptr = nullptr;
+        return cuda_fail(e, what);
+    }
+    b.bytes = want;
+    return CGH_OK;
+}
+
+// ---------------------------------------------------------- validation
+static bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+cgh_status cgh_ctx::check_problem(const float *points, const float *A,
+                                  const float *z, int N, double lambda,
+                                  double p, int Nx, int Ny, const void *out) {
+    if (N < 0 || N > CGH_MAX_POINTS)
+        return fail(CGH_ERR_INVALID_ARG, "N=%d outside [0, %d]", N, CGH_MAX_POINTS);
+    if (Nx < 1 || Ny < 1 || Nx > CGH_MAX_SIDE || Ny > CGH_MAX_SIDE)
+        return fail(CGH_ERR_INVALID_ARG, "Nx=%d, Ny=%d outside [1, %d]", Nx, Ny,
+                    CGH_MAX_SIDE);
+    if (!finite_pos(lambda) || !finite_pos(p))
+        return fail(CGH_ERR_INVALID_ARG, "lambda and p must be finite and > 0");
+    if (!out) return fail(CGH_ERR_INVALID_ARG, "output pointer is NULL");
+    if (N > 0 && (!points || !A || !z))
+        return fail(CGH_ERR_INVALID_ARG, "points, A and z must not be NULL");
+    if ((((uintptr_t)points) | ((uintptr_t)A) | ((uintptr_t)z) |
+         ((uintptr_t)out)) & 3)
+        return fail(CGH_ERR_INVALID_ARG, "float arrays must be 4-byte aligned");
+    return CGH_OK;
+}
+
+// ------------------------------------------------------------ tiles
+int cgh_ctx::pick_direct_tile(int N, int Nx, int Ny) {
+    if (forced_tile >= 0) return forced_tile;
+    auto it = tuned.find(size_bucket(CGH_DIRECT_FP32, N, Nx, Ny));
+    if (it != tuned.end()) return it->second;
+    return default_direct_tile(N, Nx, Ny, sm_count);
+}
+
+// ------------------------------------------------------- direct forward
+cgh_status cgh_ctx::forward_direct(const float *points, const float *A,
+                                   const float *z, int N, double lambda,
+                                   double p, int Nx, int Ny, float *out,
+                                   int tile_index, cudaStream_t s) {
+    DirectTile t = direct_tile_get(tile_index);
+    const int Npad = pad_to(N, t.pt);
+    const size_t rec_b = align256((size_t)Npad * sizeof(PointRec));
+    const size_t tab_f = direct_phase_table_floats(t, Npad, Nx, Ny);
+    const size_t tab_b = align256(tab_f * sizeof(float));
+    const size_t amp_b = align256((size_t)Npad * sizeof(float));
+    cgh_status st = ensure(ws, rec_b + tab_b + amp_b, s, "direct workspace");
+    if (st) return st;
+    char *base = (char *)ws.ptr;
+    PointRec *rec = (PointRec *)base;
+    int nxt = (Nx + t.tx - 1) / t.tx;
+    float *phx = (float *)(base + rec_b);
+    float *phy = phx + (size_t)nxt * Npad * t.tx;
+    float *amp = (float *)(base + rec_b + tab_b);
+
+    {
+        TimedLaunch tl(this, CGH_K_PROLOGUE, s);
+        cudaError_t e = launch_prologue(points, A, z, N, Npad, lambda, p, rec,
+                                        d_status, s);
+        if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+        tl.done();
+    }
+    {
+        TimedLaunch tl(this, CGH_K_DIRECT_TABLES, s);
+        cudaError_t e = launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp, s);
+        if (e != cudaSuccess) return cuda_fail(e, "direct tables launch");
+        tl.done();
+    }
+    {
+        TimedLaunch tl(this, CGH_K_DIRECT, s);
+        cudaError_t e = launch_direct_forward(tile_index, phx, phy, amp, Npad,
+                                              Nx, Ny, out, d_status, s);
+        if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
+        tl.done();
+    }
+    return CGH_OK;
+}
+
+cgh_status cgh_ctx::forward_naive(const float *points, const float *A,
+                                  const float *z, int N, double lambda,
+                                  double p, int Nx, int Ny, float *out,
+                                  cudaStream_t s) {
+    const size_t rec_b = align256((size_t)N * sizeof(PointRec));
+    cgh_status st = ensure(ws, rec_b, s, "naive workspace");
+    if (st) return st;
+    PointRec *rec = (PointRec *)ws.ptr;
+    {
+        TimedLaunch tl(this, CGH_K_PROLOGUE, s);
+        cudaError_t e = launch_prologue(points, A, z, N, N, lambda, p, rec,
+                                        d_status, s);
+        if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+        tl.done();
+    }
+    {
+        TimedLaunch tl(this, CGH_K_NAIVE, s);
+        cudaError_t e = launch_naive_forward(rec, N, Nx, Ny, out, s);
+        if (e != cudaSuccess) return cuda_fail(e, "naive kernel launch");
+        tl.done();
+    }
+    return CGH_OK;
+}
+
+cgh_status cgh_ctx::forward(const float *points, const float *A,
+                            const float *z, int N, double lambda, double p,
+                            int Nx, int Ny, float *out, int method,
+                            cudaStream_t s) {
+    cgh_status st = check_problem(points, A, z, N, lambda, p, Nx, Ny, out);
+    if (st) return st;
+    if (N == 0) {
+        cudaError_t e = cudaMemsetAsync(out, 0, (size_t)Nx * Ny * sizeof(float), s);
+        return e == cudaSuccess ? CGH_OK : cuda_fail(e, "cudaMemsetAsync");
+    }
+    switch (method) {
+    case CGH_DIRECT_FP32:
+        return forward_direct(points, A, z, N, lambda, p, Nx, Ny, out,
+                              pick_direct_tile(N, Nx, Ny), s);
+    case CGH_NAIVE_FP32:
+        return forward_naive(points, A, z, N, lambda, p, Nx, Ny, out, s);
+    case CGH_SEP_BF16:
+    case CGH_SEP_FP16:
+    case CGH_SEP_FP16X3:
+        return forward_separable(points, A, z, N, lambda, p, Nx, Ny, out,
+                                 method, s);
+    default:
+        return fail(CGH_ERR_INVALID_ARG, "unknown method %d", method);
+    }
+}
+
+// --------------------------------------------------------- kernel timing
+cudaEvent_t cgh_ctx::get_event() {
+    if (!event_pool.empty()) {
+        cudaEvent_t e = event_pool.back();
+        event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void cgh_ctx::timer_begin(int kernel, cudaStream_t s, cudaEvent_t *ev) {
+    (void)kernel;
+    *ev = get_event();
+    if (*ev) cudaEventRecord(*ev, s);
+}
+
+void cgh_ctx::timer_end(int kernel, cudaStream_t s, cudaEvent_t ev) {
+    if (!ev) return;
+    cudaEvent_t e1 = get_event();
+    if (!e1) {
+        event_pool.push_back(ev);
+        return;
+    }
+    cudaEventRecord(e1, s);
+    pending[kernel].push_back({ev, e1});
+}
+
+cgh_status cgh_ctx::timer_collect(int kernel) {
+    for (auto &pr : pending[kernel]) {
+        cudaError_t e = cudaEventSynchronize(pr.second);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel timing");
+        kernel_ms[kernel] += ms;
+        kernel_launches[kernel] += 1;
+        event_pool.push_back(pr.first);
+        event_pool.push_back(pr.second);
+    }
+    pending[kernel].clear();
+    return CGH_OK;
+}
+
+void cgh_ctx::timer_reset() {
+    for (int k = 0; k < CGH_K_COUNT; ++k) {
+        for (auto &pr : pending[k]) {
+            cudaEventSynchronize(pr.second);
+            event_pool.push_back(pr.first);
+            event_pool.push_back(pr.second);
+        }
+        pending[k].clear();
+        kernel_ms[k] = 0.0;
+        kernel_launches[k] = 0;
+    }
+}
+
+// ============================================================ the C ABI
+extern "C" {
+
+cgh_status cgh_create(cgh_handle *out, int device) {
+    if (!out) return CGH_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return CGH_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(device);
+    cgh_ctx *h = new (std::nothrow) cgh_ctx();
+    if (!h) return CGH_ERR_NOMEM;
+    h->device = device;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete h;
+        cudaGetLastError();
+        return CGH_ERR_CUDA;
+    }
+    h->sm_count = prop.multiProcessorCount;
+    snprintf(h->device_name, sizeof(h->device_name), "%s", prop.name);
+    h->cc_major = prop.major;
+    h->cc_minor = prop.minor;
+    if (cudaMalloc(&h->d_status, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(h->d_status, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->d_status) cudaFree(h->d_status);
+        delete h;
+        return CGH_ERR_CUDA;
+    }
+    h->load_tune_cache();
+    *out = h;
+    return CGH_OK;
+}
+
+cgh_status cgh_destroy(cgh_handle h) {
+    if (!h) return CGH_OK;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    h->release_all();
+    h->timer_reset();
+    for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+    if (h->d_status) cudaFree(h->d_status);
+    cudaGetLastError();
+    delete h;
+    return CGH_OK;
+}
+
+cgh_status cgh_forward(cgh_handle h, const float *points, const float *A,
+                       const float *z, int N, double lambda, double p, int Nx,
+                       int Ny, float *out, int method, void *stream) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    h->err[0] = 0;
+    return h->forward(points, A, z, N, lambda, p, Nx, Ny, out, method,
+                      (cudaStream_t)stream);
+}
+
+cgh_status cgh_forward_host(cgh_handle h, const float *points_host,
+                            const float *A_host, const float *z_host, int N,
+                            double lambda, double p, int Nx, int Ny,
+                            float *out_host, int method, void *stream) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    h->err[0] = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    cgh_status st = h->check_problem(points_host, A_host, z_host, N, lambda, p,
+                                     Nx, Ny, out_host);
+    if (st) return st;
+    const size_t pts_b = align256((size_t)N * 2 * sizeof(float));
+    const size_t n_b = align256((size_t)N * sizeof(float));
+    const size_t out_b = align256((size_t)Nx * Ny * sizeof(float));
+    st = h->ensure(h->io, pts_b + 2 * n_b + out_b, s, "host-call staging");
+    if (st) return st;
+    char *base = (char *)h->io.ptr;
+    float *d_pts = (float *)base, *d_A = (float *)(base + pts_b);
+    float *d_z = (float *)(base + pts_b + n_b);
+    float *d_out = (float *)(base + pts_b + 2 * n_b);
+    cudaError_t e = cudaSuccess;
+    if (N > 0) {
+        e = cudaMemcpyAsync(d_pts, points_host, (size_t)N * 2 * sizeof(float),
+                            cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_A, A_host, (size_t)N * sizeof(float),
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_z, z_host, (size_t)N * sizeof(float),
+                                cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return h->cuda_fail(e, "host-to-device copy");
+    }
+    st = h->forward(d_pts, d_A, d_z, N, lambda, p, Nx, Ny, d_out, method, s);
+    if (st) return st;
+    e = cudaMemcpyAsync(out_host, d_out, (size_t)Nx * Ny * sizeof(float),
+                        cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return h->cuda_fail(e, "device-to-host copy");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaStreamSynchronize");
+    return CGH_OK;
+}
+
+cgh_status cgh_last_device_status(cgh_handle h, void *stream) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaStreamSynchronize");
+    unsigned v = 0;
+    e = cudaMemcpy(&v, h->d_status, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return h->cuda_fail(e, "device status read");
+    if (v & DEV_TIMEOUT)
+        return h->fail(CGH_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (v & DEV_BOUNDS)
+        return h->fail(CGH_ERR_CUDA, "a device bounds check failed");
+    if (v & DEV_BAD_POINT)
+        return h->fail(CGH_ERR_INVALID_ARG,
+                       "a point had z <= 0 or a non-finite value; it was skipped");
+    return CGH_OK;
+}
+
+uint64_t cgh_launch_count(cgh_handle h) { return h ? h->launches : 0; }
+
+cgh_status cgh_kernel_timing(cgh_handle h, int enable) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    h->timer_reset();
+    h->timing = enable != 0;
+    return CGH_OK;
+}
+
+cgh_status cgh_kernel_time(cgh_handle h, int kernel, double *total_ms,
+                           uint64_t *launches) {
+    if (!h || kernel < 0 || kernel >= CGH_K_COUNT) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cgh_status st = h->timer_collect(kernel);
+    if (st) return st;
+    if (total_ms) *total_ms = h->kernel_ms[kernel];
+    if (launches) *launches = h->kernel_launches[kernel];
+    return CGH_OK;
+}
+
+const char *cgh_status_string(int status) {
+    switch (status) {
+    case CGH_OK: return "CGH_OK";
+    case CGH_ERR_INVALID_ARG: return "CGH_ERR_INVALID_ARG: invalid argument";
+    case CGH_ERR_CUDA: return "CGH_ERR_CUDA: a CUDA call failed";
+    case CGH_ERR_NOMEM: return "CGH_ERR_NOMEM: out of device memory";
+    case CGH_ERR_UNSUPPORTED: return "CGH_ERR_UNSUPPORTED: not supported";
+    case CGH_ERR_TIMEOUT: return "CGH_ERR_TIMEOUT: a device wait timed out";
+    default: return "unknown cgh_status";
+    }
+}
+
+const char *cgh_last_error(cgh_handle h) { return h ? h->err : ""; }
+
+int cgh_direct_tile_count(void) { return direct_tile_count(); }
+
+cgh_status cgh_direct_tile_get(int i, cgh_direct_tile *out) {
+    if (!out || i < 0 || i >= direct_tile_count()) return CGH_ERR_INVALID_ARG;
+    DirectTile t = direct_tile_get(i);
+    out->tile_x = t.tx;
+    out->tile_y = t.ty;
+    out->vec_x = t.vx;
+    out->vec_y = t.vy;
+    out->points_per_stage = t.pt;
+    return CGH_OK;
+}
+
+cgh_status cgh_set_direct_tile(cgh_handle h, const cgh_direct_tile *tile) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    if (!tile) {
+        h->forced_tile = -1;
+        return CGH_OK;
+    }
+    DirectTile t{tile->tile_x, tile->tile_y, tile->vec_x, tile->vec_y,
+                 tile->points_per_stage};
+    int i = direct_tile_index(t);
+    if (i < 0)
+        return h->fail(CGH_ERR_UNSUPPORTED, "tile %dx%d/%dx%d/%d not compiled in",
+                       t.tx, t.ty, t.vx, t.vy, t.pt);
+    h->forced_tile = i;
+    return CGH_OK;
+}
+
+}  // extern "C"

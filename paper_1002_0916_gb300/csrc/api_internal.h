@@ -1,0 +1,100 @@
+// api_internal.h -- the handle behind cgh_handle (internal to libcgh).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "cgh.h"
+
+#define CGH_MAX_POINTS (1 << 24)
+#define CGH_MAX_SIDE 32768
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Buffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct cgh_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    char device_name[256] = {0};
+    char err[512] = {0};
+    unsigned *d_status = nullptr;  // device status word (DEV_* bits)
+    uint64_t launches = 0;         // kernels launched by this handle
+
+    Buffer ws;    // forward workspace: point records and tables
+    Buffer ws2;   // second workspace: split planes / backward / batch
+    Buffer io;    // staging for cgh_forward_host
+    Buffer part;  // partial sums of the adjoint
+    Buffer meta;  // small per-call metadata (tensor maps, work lists)
+
+    // kernel timing (cgh_kernel_timing / cgh_kernel_time)
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[CGH_K_COUNT];
+    std::vector<cudaEvent_t> event_pool;
+    double kernel_ms[CGH_K_COUNT] = {0};
+    uint64_t kernel_launches[CGH_K_COUNT] = {0};
+    cudaEvent_t get_event();
+    void timer_begin(int kernel, cudaStream_t s, cudaEvent_t *ev);
+    void timer_end(int kernel, cudaStream_t s, cudaEvent_t ev);
+    cgh_status timer_collect(int kernel);
+    void timer_reset();
+
+    int forced_tile = -1;                         // direct tile override
+    std::unordered_map<std::string, int> tuned;   // size bucket -> tile
+
+    cgh_status fail(cgh_status st, const char *fmt, ...);
+    cgh_status cuda_fail(cudaError_t e, const char *where);
+    cgh_status ensure(Buffer &b, size_t bytes, cudaStream_t s, const char *what);
+    cgh_status check_problem(const float *points, const float *A, const float *z,
+                             int N, double lambda, double p, int Nx, int Ny,
+                             const void *out);
+    int pick_direct_tile(int N, int Nx, int Ny);
+
+    cgh_status forward(const float *points, const float *A, const float *z,
+                       int N, double lambda, double p, int Nx, int Ny,
+                       float *out, int method, cudaStream_t s);
+    cgh_status forward_direct(const float *points, const float *A,
+                              const float *z, int N, double lambda, double p,
+                              int Nx, int Ny, float *out, int tile_index,
+                              cudaStream_t s);
+    cgh_status forward_naive(const float *points, const float *A,
+                             const float *z, int N, double lambda, double p,
+                             int Nx, int Ny, float *out, cudaStream_t s);
+    cgh_status forward_separable(const float *points, const float *A,
+                                 const float *z, int N, double lambda, double p,
+                                 int Nx, int Ny, float *out, int method,
+                                 cudaStream_t s);
+
+    void load_tune_cache();
+    void release_all();
+};
+
+// autotune.cu
+std::string size_bucket(int method, int N, int Nx, int Ny);
+int default_direct_tile(int N, int Nx, int Ny, int sm_count);
+
+// Brackets one kernel launch with events when the handle's timing is on,
+// and counts the launch.
+struct TimedLaunch {
+    cgh_ctx *h;
+    int kernel;
+    cudaStream_t s;
+    cudaEvent_t ev = nullptr;
+    TimedLaunch(cgh_ctx *h_, int k, cudaStream_t s_) : h(h_), kernel(k), s(s_) {
+        if (h->timing) h->timer_begin(kernel, s, &ev);
+    }
+    void done() {
+        ++h->launches;
+        if (h->timing) h->timer_end(kernel, s, ev);
+    }
+};

@@ -1,0 +1,176 @@
+// autotune.cu -- tile-shape choice for the direct kernel: a wave-count
+// heuristic by default, and a measuring autotuner (cgh_tune) whose choices
+// are kept per size bucket in the handle and, optionally, in a JSON-lines
+// cache file named by CGH_TUNE_CACHE.
+//
+// The paper fixed its shapes at compile time (16 x 16 items per group,
+// 256 points per shared-memory stage, Section 2); here the best shape
+// depends on how many CTAs a frame gives relative to the 152 SMs.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "api_internal.h"
+#include "common.cuh"
+
+using namespace cgh;
+
+std::string size_bucket(int method, int N, int Nx, int Ny) {
+    int nb = 1;
+    while (nb < N) nb <<= 1;
+    char buf[96];
+    snprintf(buf, sizeof(buf), "m%d_n%d_x%d_y%d", method, nb, (Nx + 63) / 64 * 64,
+             (Ny + 63) / 64 * 64);
+    return buf;
+}
+
+int default_direct_tile(int N, int Nx, int Ny, int sm_count) {
+    (void)N;
+    const int resident = 3;  // CTAs of 256 threads per SM, typical
+    double best = 1e300;
+    int best_i = 0;
+    for (int i = 0; i < direct_tile_count(); ++i) {
+        DirectTile t = direct_tile_get(i);
+        long long ctas = (long long)((Nx + t.tx - 1) / t.tx) * ((Ny + t.ty - 1) / t.ty);
+        long long slots = (long long)sm_count * resident;
+        long long waves = (ctas + slots - 1) / slots;
+        // work per CTA, plus shared-memory loads per pixel update
+        double cost = (double)waves * t.tx * t.ty *
+                      (1.0 + 0.25 / (t.vx * t.vy) + 0.25 / t.pt);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_i = i;
+        }
+    }
+    return best_i;
+}
+
+// Fill a synthetic cloud for timing: positions spread over the frame,
+// z in [0.5, 1.5] m.  Values only shape the timing, not a result.
+__global__ void tune_fill_kernel(float *pts, float *A, float *z, int N, int Nx,
+                                 int Ny) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    unsigned hsh = (unsigned)j * 2654435761u;
+    pts[2 * j] = (float)(hsh % (unsigned)Nx);
+    pts[2 * j + 1] = (float)((hsh >> 11) % (unsigned)Ny);
+    A[j] = 0.5f;
+    z[j] = 0.5f + (float)(hsh & 1023) / 1023.0f;
+}
+
+static const char *cache_path() {
+    const char *p = getenv("CGH_TUNE_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+
+void cgh_ctx::load_tune_cache() {
+    const char *path = cache_path();
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char line[1024];
+    while (fgets(line, sizeof(line), f)) {
+        char dev[256] = {0}, bucket[128] = {0};
+        int tx, ty, vx, vy, pt;
+        // {"device": "...", "bucket": "...", "tile": [tx, ty, vx, vy, pt]}
+        const char *d = strstr(line, "\"device\": \"");
+        const char *b = strstr(line, "\"bucket\": \"");
+        const char *t = strstr(line, "\"tile\": [");
+        if (!d || !b || !t) continue;
+        if (sscanf(d + 11, "%255[^\"]", dev) != 1) continue;
+        if (sscanf(b + 11, "%127[^\"]", bucket) != 1) continue;
+        if (sscanf(t + 9, "%d , %d , %d , %d , %d", &tx, &ty, &vx, &vy, &pt) != 5)
+            continue;
+        if (strcmp(dev, device_name) != 0) continue;
+        int i = direct_tile_index(DirectTile{tx, ty, vx, vy, pt});
+        if (i >= 0) tuned[bucket] = i;
+    }
+    fclose(f);
+}
+
+extern "C" cgh_status cgh_tune(cgh_handle h, int N, int Nx, int Ny, int method,
+                               void *stream, cgh_direct_tile *chosen) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    if (method != CGH_DIRECT_FP32)
+        return h->fail(CGH_ERR_UNSUPPORTED,
+                       "only the direct method has tunable tiles");
+    if (N < 1 || N > CGH_MAX_POINTS || Nx < 1 || Ny < 1 || Nx > CGH_MAX_SIDE ||
+        Ny > CGH_MAX_SIDE)
+        return h->fail(CGH_ERR_INVALID_ARG, "bad tuning size");
+    int prev_dev = 0;
+    cudaGetDevice(&prev_dev);
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t in_b = align256((size_t)N * 4 * sizeof(float));
+    const size_t out_b = align256((size_t)Nx * Ny * sizeof(float));
+    cgh_status st = h->ensure(h->ws2, in_b + out_b, s, "tuning buffers");
+    if (st) {
+        cudaSetDevice(prev_dev);
+        return st;
+    }
+    float *pts = (float *)h->ws2.ptr;
+    float *A = pts + 2 * (size_t)N, *z = pts + 3 * (size_t)N;
+    float *out = (float *)((char *)h->ws2.ptr + in_b);
+    {
+        TimedLaunch tl(h, CGH_K_AUX, s);
+        tune_fill_kernel<<<(N + 127) / 128, 128, 0, s>>>(pts, A, z, N, Nx, Ny);
+        tl.done();
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best_i = -1;
+    for (int i = 0; i < direct_tile_count(); ++i) {
+        // one warm-up, then the best of three
+        st = h->forward_direct(pts, A, z, N, 532e-9, 8e-6, Nx, Ny, out, i, s);
+        if (st) break;
+        float ms_i = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            cudaEventRecord(e0, s);
+            st = h->forward_direct(pts, A, z, N, 532e-9, 8e-6, Nx, Ny, out, i, s);
+            cudaEventRecord(e1, s);
+            if (st) break;
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < ms_i) ms_i = ms;
+        }
+        if (st) break;
+        if (ms_i < best_ms) {
+            best_ms = ms_i;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaGetLastError();
+    if (st == CGH_OK && e != cudaSuccess) st = h->cuda_fail(e, "tuning");
+    if (st == CGH_OK && best_i >= 0) {
+        std::string b = size_bucket(CGH_DIRECT_FP32, N, Nx, Ny);
+        h->tuned[b] = best_i;
+        DirectTile t = direct_tile_get(best_i);
+        if (chosen) {
+            chosen->tile_x = t.tx;
+            chosen->tile_y = t.ty;
+            chosen->vec_x = t.vx;
+            chosen->vec_y = t.vy;
+            chosen->points_per_stage = t.pt;
+        }
+        if (const char *path = cache_path()) {
+            if (FILE *f = fopen(path, "a")) {
+                fprintf(f,
+                        "{\"device\": \"%s\", \"bucket\": \"%s\", \"tile\": "
+                        "[%d, %d, %d, %d, %d], \"ms\": %.5f}\n",
+                        h->device_name, b.c_str(), t.tx, t.ty, t.vx, t.vy, t.pt,
+                        best_ms);
+                fclose(f);
+            }
+        }
+    }
+    cudaSetDevice(prev_dev);
+    return st;
+}

@@ -1,0 +1,158 @@
+// common.cuh -- internal declarations and PTX helpers shared by the CUDA
+// translation units of libcgh (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cgh.h"
+
+namespace cgh {
+
+// Bits of the device status word.
+enum : unsigned {
+    DEV_BAD_POINT = 1u,   // a point had z <= 0 or a non-finite coordinate
+    DEV_TIMEOUT = 2u,     // a bounded wait gave up
+    DEV_BOUNDS = 4u       // an internal bounds check failed
+};
+
+// Per-point record built by the prologue (Section 1, Eq. 1).  The phase of
+// point j at pixel (x, y), in turns, is
+//     Q_j ((x - x_j)^2 + (y - y_j)^2),   Q_j = P_j / (2 pi) = p^2 / (2 lambda z_j),
+// and each axis part expands to c x^2 - b x + a (mod 1) with
+//     c = frac(Q_j), b = frac(2 Q_j x_j), a = frac(Q_j x_j^2).
+// All three are stored as unsigned 0.64 fixed-point turns, so that the
+// per-pixel evaluation is exact integer arithmetic modulo 1 turn.
+struct PointRec {
+    uint64_t c;
+    uint64_t bx, ax;
+    uint64_t by, ay;
+    float A;       // amplitude (0 for rejected points)
+    float Q32;     // Q_j rounded to FP32 (diagnostics)
+};
+static_assert(sizeof(PointRec) == 48, "PointRec layout");
+
+// Axis phase in 0.64 turns at integer coordinate u: c u^2 - b u + a (mod 1).
+__device__ __forceinline__ uint64_t axis_phase(uint64_t c, uint64_t b,
+                                               uint64_t a, int u) {
+    uint64_t uu = (uint64_t)((int64_t)u * (int64_t)u);
+    return c * uu - b * (uint64_t)(int64_t)u + a;
+}
+
+// Top 32 bits of a 0.64 phase as a signed turn count in [-1/2, 1/2).
+__device__ __forceinline__ int phase_hi(uint64_t ph) { return (int)(ph >> 32); }
+
+// 2 pi / 2^32: radians per unit of a signed 0.32 phase.
+constexpr float RAD_PER_U32 = 1.4629180792671596e-9f;
+// 1 / 2^32: turns per unit of a signed 0.32 phase.
+constexpr float TURN_PER_U32 = 2.3283064365386963e-10f;
+
+// ---------------------------------------------------------------- PTX
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar,
+                                                      uint32_t bytes) {
+    asm volatile(
+        "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// About one second at the GB300's clocks.
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;
+
+// Wait for phase `parity` of `bar` to complete, giving up after
+// WAIT_LIMIT_CYCLES.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar,
+                                                  uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+    }
+    return true;
+}
+
+// 1-D bulk copy global -> shared, completing `bytes` on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src,
+                                         uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void set_status(unsigned *status, unsigned bits) {
+    if (status) atomicOr(status, bits);
+}
+
+}  // namespace cgh
+
+// ------------------------------------------------ launchers (host side)
+namespace cgh {
+
+struct DirectTile {
+    int tx, ty, vx, vy, pt;
+};
+
+// Number of points after padding to a multiple of `pt`.
+inline int pad_to(int n, int m) { return (n + m - 1) / m * m; }
+
+// prologue.cu
+cudaError_t launch_prologue(const float *points, const float *A,
+                            const float *z, int N, int Npad, double lambda,
+                            double p, PointRec *rec, unsigned *status,
+                            cudaStream_t s);
+
+// direct.cu
+int direct_tile_count();
+DirectTile direct_tile_get(int i);
+int direct_tile_index(const DirectTile &t);
+size_t direct_phase_table_floats(const DirectTile &t, int Npad, int Nx, int Ny);
+cudaError_t launch_direct_tables(const PointRec *rec, int Npad, int Nx, int Ny,
+                                 const DirectTile &t, float *phx, float *phy,
+                                 float *amp, cudaStream_t s);
+cudaError_t launch_direct_forward(int tile_index, const float *phx,
+                                  const float *phy, const float *amp, int Npad,
+                                  int Nx, int Ny, float *out, unsigned *status,
+                                  cudaStream_t s);
+cudaError_t launch_naive_forward(const PointRec *rec, int N, int Nx, int Ny,
+                                 float *out, cudaStream_t s);
+
+}  // namespace cgh
