@@ -147,6 +147,43 @@ typedef struct {
 cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int count,
                      int method, void *stream);
 
+/* Size in bytes of the fixed device scratch array behind
+ * cgh_forward_noalloc (16 MiB, present on every GPU that loads this
+ * library, for the life of the process). */
+#define CGH_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate GPU memory while they run -- for example a display
+ * loop driving a spatial light modulator at a fixed frame rate (cudaMalloc
+ * can take unbounded time, cudaFree stalls the whole device), or a plug-in
+ * inside an application that owns all device memory itself.  They cannot
+ * create a cgh_handle, so this call needs none.
+ *
+ * Computes the same hologram as cgh_forward(..., CGH_DIRECT_FP32, ...) on
+ * the calling thread's current device, using the same kernels, but takes
+ * all scratch (point records, angle tables, status word) from one fixed
+ * __device__ array of CGH_NOALLOC_SCRATCH_BYTES.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.  points, A, z, out: device memory
+ * owned by the caller, layouts as cgh_forward; stream: cudaStream_t or NULL.
+ * Asynchronous on `stream`.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and remembers it; make that first call before any
+ * stream capture.  Every call on a device shares the array and leaves its
+ * contents behind; each call clears what it needs cleared, but calls whose
+ * work overlaps on the GPU (other streams, other threads) race on the array
+ * and must be serialised by the caller.  Points with z <= 0 or non-finite
+ * values are skipped; there is no status read-back in this variant.
+ *
+ * Returns CGH_OK; CGH_ERR_INVALID_ARG for the argument errors cgh_forward
+ * rejects; CGH_ERR_UNSUPPORTED when the frame needs more scratch than the
+ * array holds (about (Nx + Ny) * N * 4 bytes of angle tables plus 52 bytes
+ * per point, with Nx, Ny rounded up to 64 and N to 32) -- nothing is
+ * launched then; CGH_ERR_CUDA if a CUDA call fails. */
+cgh_status cgh_forward_noalloc(const float *points, const float *A,
+                               const float *z, int N, double lambda, double p,
+                               int Nx, int Ny, float *out, void *stream);
+
 /* Tile shape of the direct kernel. */
 typedef struct {
     int tile_x;            /* pixels per CTA along x           */

@@ -89,6 +89,8 @@ def _load():
     L.cgh_last_error.argtypes = [vp]
     L.cgh_last_error.restype = ctypes.c_char_p
     L.cgh_debug_gemm.argtypes = [vp, fp, fp, fp, ci, ci, ci, ci, vp]
+    L.cgh_forward_noalloc.argtypes = [fp, fp, fp, ci, cd, cd, ci, ci, fp, vp]
+    L.cgh_forward_noalloc.restype = ci
     L.cgh_kernel_timing.argtypes = [vp, ci]
     L.cgh_kernel_time.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_uint64)]
