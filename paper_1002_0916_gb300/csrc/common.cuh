@@ -155,4 +155,25 @@ cudaError_t launch_direct_forward(int tile_index, const float *phx,
 cudaError_t launch_naive_forward(const PointRec *rec, int N, int Nx, int Ny,
                                  float *out, cudaStream_t s);
 
+// umma.cu: D = A B^T (single pass) or Ahi Bhi^T + lo_scale (Ahi Blo^T +
+// Alo Bhi^T) (split) on the tensor cores.  A: M x K, B: N x K, 16-bit,
+// K-major with row strides lda, ldb (elements); D: FP32, row stride ldd.
+struct GemmOperands {
+    const void *A_hi, *A_lo, *B_hi, *B_lo;
+    int M, N, K;
+    long long lda, ldb;
+    bool bf16, split;
+    float lo_scale;
+    float *D;
+    long long ldd;
+};
+bool gemm_operands_ok(const GemmOperands &op);
+cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
+                             cudaStream_t s);
+
+// separable.cu: U / V tables of the separable form.
+cudaError_t launch_sep_tables(const PointRec *rec, int N, int Npad, int Nx,
+                              int Ny, int Kp, int kind, void *Lhi, void *Llo,
+                              void *Rhi, void *Rlo, cudaStream_t s);
+
 }  // namespace cgh

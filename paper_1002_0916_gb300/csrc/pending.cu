@@ -2,12 +2,6 @@
 #include "api_internal.h"
 #include "common.cuh"
 
-cgh_status cgh_ctx::forward_separable(const float *, const float *,
-                                      const float *, int, double, double, int,
-                                      int, float *, int method, cudaStream_t) {
-    return fail(CGH_ERR_UNSUPPORTED, "separable method %d not built yet", method);
-}
-
 void cgh_ctx::release_all() {
     for (Buffer *b : {&ws, &ws2, &io, &part, &meta}) {
         if (b->ptr) cudaFree(b->ptr);
@@ -29,12 +23,6 @@ cgh_status cgh_backward(cgh_handle h, const float *, const float *,
 cgh_status cgh_batch(cgh_handle h, const cgh_problem *, int, int, void *) {
     if (!h) return CGH_ERR_INVALID_ARG;
     return h->fail(CGH_ERR_UNSUPPORTED, "batch not built yet");
-}
-
-cgh_status cgh_debug_gemm(cgh_handle h, const void *, const void *, float *,
-                          int, int, int, int, void *) {
-    if (!h) return CGH_ERR_INVALID_ARG;
-    return h->fail(CGH_ERR_UNSUPPORTED, "tensor-core GEMM not built yet");
 }
 
 }  // extern "C"

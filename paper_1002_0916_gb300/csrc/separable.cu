@@ -1,0 +1,196 @@
+// separable.cu -- the separable form of Eq. 1 on the tensor cores (steps
+// A6-A7).
+//
+// The phase of Eq. 1 is a sum of an x part and a y part, so
+//     I(x, y) = sum_j A_j cos(th_x(x, j) + th_y(y, j))
+//             = sum_j [A_j cos th_x][cos th_y] - [A_j sin th_x][sin th_y]
+//             = Re(U diag(A) V^T)[x, y],  U = e^{i th_x}, V = e^{i th_y},
+// with th_u(u, j) = P_j (u - u_j)^2 (exact: no approximation).  Written with
+// interleaved real pairs along K = 2N,
+//     L[x][2j] = A_j cos th_x,  L[x][2j+1] = -A_j sin th_x   (Nx x K)
+//     R[y][2j] =     cos th_y,  R[y][2j+1] =      sin th_y   (Ny x K)
+// the hologram is the plain product I = R L^T (Ny x Nx, row-major), a dense
+// contraction of depth 2N run by the tcgen05 GEMM of umma.cu.
+//
+// Tables: the axis phase is evaluated exactly in 64-bit fixed-point turns
+// from the point records (prologue.cu), its top 32 bits give the angle, and
+// sincospif gives the pair.  Entries for padding points (j >= N) are 0.
+// Precision variants:
+//   kind 0  BF16 single pass   (one plane per table)
+//   kind 1  FP16 single pass
+//   kind 2  FP16 split: hi = fp16(v), lo = fp16((v - hi) * 2^12); the GEMM
+//           forms hi*hi + 2^-12 (hi*lo + lo*hi) with FP32 accumulation.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "api_internal.h"
+#include "common.cuh"
+
+namespace cgh {
+
+constexpr float LO_SCALE = 4096.0f;  // 2^12: lo planes stored scaled up
+
+template <int KIND>
+__global__ void sep_tables_kernel(const PointRec *__restrict__ rec, int N,
+                                  int Npad, int Nx, int Ny, int Kp,
+                                  void *__restrict__ Lhi, void *__restrict__ Llo,
+                                  void *__restrict__ Rhi,
+                                  void *__restrict__ Rlo) {
+    const long long total = (long long)(Nx + Ny) * (Kp / 2);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / (Kp / 2));
+        const int j = (int)(e - (long long)r * (Kp / 2));
+        const bool is_x = r < Nx;
+        const int u = is_x ? r : r - Nx;
+        float re = 0.0f, im = 0.0f;
+        if (j < N) {
+            const PointRec pr = rec[j];
+            const uint64_t ph = is_x ? axis_phase(pr.c, pr.bx, pr.ax, u)
+                                     : axis_phase(pr.c, pr.by, pr.ay, u);
+            const float turns = (float)phase_hi(ph) * TURN_PER_U32;
+            float s, c;
+            sincospif(2.0f * turns, &s, &c);
+            if (is_x) {
+                re = pr.A * c;
+                im = -pr.A * s;
+            } else {
+                re = c;
+                im = s;
+            }
+        }
+        const size_t off = (size_t)u * Kp + 2 * (size_t)j;
+        void *hi_base = is_x ? Lhi : Rhi;
+        if (KIND == 0) {
+            *reinterpret_cast<__nv_bfloat162 *>((__nv_bfloat16 *)hi_base + off) =
+                __floats2bfloat162_rn(re, im);
+        } else {
+            const __half2 h = __floats2half2_rn(re, im);
+            *reinterpret_cast<__half2 *>((__half *)hi_base + off) = h;
+            if (KIND == 2) {
+                const float2 hf = __half22float2(h);
+                void *lo_base = is_x ? Llo : Rlo;
+                *reinterpret_cast<__half2 *>((__half *)lo_base + off) =
+                    __floats2half2_rn((re - hf.x) * LO_SCALE, (im - hf.y) * LO_SCALE);
+            }
+        }
+    }
+}
+
+cudaError_t launch_sep_tables(const PointRec *rec, int N, int Npad, int Nx,
+                              int Ny, int Kp, int kind, void *Lhi, void *Llo,
+                              void *Rhi, void *Rlo, cudaStream_t s) {
+    const long long total = (long long)(Nx + Ny) * (Kp / 2);
+    const int threads = 256;
+    long long blocks = (total + threads - 1) / threads;
+    if (blocks > 152LL * 32) blocks = 152LL * 32;
+    if (kind == 0)
+        sep_tables_kernel<0><<<(int)blocks, threads, 0, s>>>(rec, N, Npad, Nx, Ny,
+                                                             Kp, Lhi, Llo, Rhi, Rlo);
+    else if (kind == 1)
+        sep_tables_kernel<1><<<(int)blocks, threads, 0, s>>>(rec, N, Npad, Nx, Ny,
+                                                             Kp, Lhi, Llo, Rhi, Rlo);
+    else
+        sep_tables_kernel<2><<<(int)blocks, threads, 0, s>>>(rec, N, Npad, Nx, Ny,
+                                                             Kp, Lhi, Llo, Rhi, Rlo);
+    return cudaGetLastError();
+}
+
+}  // namespace cgh
+
+using namespace cgh;
+
+cgh_status cgh_ctx::forward_separable(const float *points, const float *A,
+                                      const float *z, int N, double lambda,
+                                      double p, int Nx, int Ny, float *out,
+                                      int method, cudaStream_t s) {
+    const int kind = method == CGH_SEP_BF16 ? 0 : method == CGH_SEP_FP16 ? 1 : 2;
+    const bool split = kind == 2;
+    const int Kp = pad_to(2 * N, 64);
+    const int Npad = Kp / 2;
+    const size_t rec_b = align256((size_t)Npad * sizeof(PointRec));
+    const size_t l_b = align256((size_t)Nx * Kp * 2);
+    const size_t r_b = align256((size_t)Ny * Kp * 2);
+    const size_t planes = split ? 2 : 1;
+    cgh_status st = ensure(ws, rec_b + planes * (l_b + r_b), s, "separable workspace");
+    if (st) return st;
+    char *base = (char *)ws.ptr;
+    PointRec *rec = (PointRec *)base;
+    void *Lhi = base + rec_b;
+    void *Rhi = base + rec_b + l_b;
+    void *Llo = split ? base + rec_b + l_b + r_b : nullptr;
+    void *Rlo = split ? base + rec_b + 2 * l_b + r_b : nullptr;
+    {
+        TimedLaunch tl(this, CGH_K_PROLOGUE, s);
+        cudaError_t e = launch_prologue(points, A, z, N, Npad, lambda, p, rec,
+                                        d_status, s);
+        if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+        tl.done();
+    }
+    {
+        TimedLaunch tl(this, CGH_K_SEP_TABLES, s);
+        cudaError_t e = launch_sep_tables(rec, N, Npad, Nx, Ny, Kp, kind, Lhi, Llo,
+                                          Rhi, Rlo, s);
+        if (e != cudaSuccess) return cuda_fail(e, "separable tables launch");
+        tl.done();
+    }
+    GemmOperands op{};
+    op.A_hi = Rhi;
+    op.A_lo = Rlo;
+    op.B_hi = Lhi;
+    op.B_lo = Llo;
+    op.M = Ny;
+    op.N = Nx;
+    op.K = Kp;
+    op.lda = Kp;
+    op.ldb = Kp;
+    op.bf16 = kind == 0;
+    op.split = split;
+    op.lo_scale = 1.0f / LO_SCALE;
+    op.D = out;
+    op.ldd = Nx;
+    {
+        TimedLaunch tl(this, CGH_K_GEMM, s);
+        cudaError_t e = launch_umma_gemm(op, d_status, s);
+        if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
+        tl.done();
+    }
+    return CGH_OK;
+}
+
+extern "C" cgh_status cgh_debug_gemm(cgh_handle h, const void *A, const void *B,
+                                     float *D, int M, int N, int K, int is_bf16,
+                                     void *stream) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    GemmOperands op{};
+    op.A_hi = A;
+    op.B_hi = B;
+    op.M = M;
+    op.N = N;
+    op.K = K;
+    op.lda = K;
+    op.ldb = K;
+    op.bf16 = is_bf16 != 0;
+    op.split = false;
+    op.lo_scale = 0.0f;
+    op.D = D;
+    op.ldd = N;
+    if (!A || !B || !D || !gemm_operands_ok(op))
+        return h->fail(CGH_ERR_INVALID_ARG,
+                       "debug GEMM: need M, N >= 1, K a positive multiple of 64, "
+                       "16-byte aligned A and B");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cgh_status st = CGH_OK;
+    {
+        TimedLaunch tl(h, CGH_K_GEMM, (cudaStream_t)stream);
+        cudaError_t e = launch_umma_gemm(op, h->d_status, (cudaStream_t)stream);
+        if (e != cudaSuccess)
+            st = h->cuda_fail(e, "tensor-core GEMM launch");
+        else
+            tl.done();
+    }
+    cudaSetDevice(prev);
+    return st;
+}

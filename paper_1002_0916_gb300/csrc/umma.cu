@@ -1,0 +1,301 @@
+// umma.cu -- the tensor-core GEMM of the separable methods (step A7):
+//
+//     D[m][n] = sum_k A[m][k] B[n][k]                      (single pass)
+//     D[m][n] = sum_k Ahi Bhi + s * (Ahi Blo + Alo Bhi)    (split, s = 2^-12)
+//
+// A, B: 16-bit (FP16 or BF16), K-major; D: FP32 row-major.
+//
+// One CTA computes a 128 x BN tile of D with tcgen05.mma (kind::f16,
+// cta_group::1) accumulating in tensor memory (TMEM).  Warp roles:
+//   warp 0      TMA producer: 2-D tiled loads (128-byte swizzle) of the
+//               K-blocks of A and B into a STAGES-deep shared-memory ring,
+//               completing on `full` mbarriers;
+//   warp 1      allocates TMEM; its lane 0 issues the MMAs (4 per 64-wide
+//               K-block per product) and releases ring slots through
+//               tcgen05.commit -> `empty` mbarriers;
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator(s), combine, store.
+// The split form keeps two accumulators (hi*hi and the two cross terms),
+// so the lo planes can be stored pre-scaled by 2^12 and stay normal FP16
+// numbers; the epilogue adds them back with the factor 2^-12.
+// Every mbarrier wait is bounded; a timeout raises DEV_TIMEOUT, the CTA
+// skips its store, waits (bounded) for its own copies, frees TMEM and exits.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "api_internal.h"
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace cgh {
+
+struct GemmArgs {
+    int M, N, K;
+    float *D;
+    long long ldd;
+    float lo_scale;
+    unsigned *status;
+};
+
+template <int BN, bool SPLIT, int STAGES>
+struct GemmShape {
+    static constexpr int BM = 128, BK = 64;
+    static constexpr uint32_t A_BYTES = BM * BK * 2;
+    static constexpr uint32_t B_BYTES = BN * BK * 2;
+    static constexpr uint32_t STAGE_BYTES =
+        SPLIT ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
+    static constexpr uint32_t TMEM_COLS = SPLIT ? 2 * BN : BN;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "UMMA N");
+    static_assert(TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256 ||
+                      TMEM_COLS == 512,
+                  "TMEM allocation must be a power of two >= 32 columns");
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+template <int BN, bool SPLIT, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
+                 const __grid_constant__ CUtensorMap tB,
+                 const __grid_constant__ CUtensorMap tA2,
+                 const __grid_constant__ CUtensorMap tB2, GemmArgs g,
+                 uint32_t idesc) {
+    using S = GemmShape<BN, SPLIT, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[STAGES];
+    __shared__ __align__(8) uint64_t empty[STAGES];
+    __shared__ __align__(8) uint64_t accum_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * S::BM;
+    const int KB = g.K / S::BK;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&accum_bar, 1);
+        mbar_fence_init();
+        umma::prefetch_tmap(&tA);
+        umma::prefetch_tmap(&tB);
+        if (SPLIT) {
+            umma::prefetch_tmap(&tA2);
+            umma::prefetch_tmap(&tB2);
+        }
+    }
+    if (warp == 1) {
+        umma::tmem_alloc(&tmem_base, S::TMEM_COLS);
+        umma::tmem_relinquish();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------- producer
+        int issued = 0;
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES &&
+                !mbar_wait_bounded(&empty[s], (uint32_t)(((kb / STAGES) - 1) & 1))) {
+                abort_flag = 1;
+                set_status(g.status, DEV_TIMEOUT);
+            }
+            if (abort_flag) break;
+            uint8_t *st = smem + (size_t)s * S::STAGE_BYTES;
+            mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
+            umma::tma_load_2d(st, &tA, kb * S::BK, m0, &full[s]);
+            umma::tma_load_2d(st + S::A_BYTES, &tB, kb * S::BK, n0, &full[s]);
+            if (SPLIT) {
+                umma::tma_load_2d(st + S::A_BYTES + S::B_BYTES, &tA2, kb * S::BK,
+                                  m0, &full[s]);
+                umma::tma_load_2d(st + 2 * S::A_BYTES + S::B_BYTES, &tB2,
+                                  kb * S::BK, n0, &full[s]);
+            }
+            ++issued;
+        }
+        if (abort_flag) {
+            // let this CTA's own copies land before its shared memory goes
+            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+                mbar_wait_bounded(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
+        }
+    } else if (warp == 1 && lane == 0) {
+        // --------------------------------------------------- MMA issuer
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((kb / STAGES) & 1))) {
+                abort_flag = 1;
+                set_status(g.status, DEV_TIMEOUT);
+            }
+            if (abort_flag) break;
+            umma::fence_after_sync();
+            const uint32_t a = smem_u32(smem + (size_t)s * S::STAGE_BYTES);
+            const uint32_t b = a + S::A_BYTES;
+            const uint64_t ad = umma::sw128_kmajor_desc(a);
+            const uint64_t bd = umma::sw128_kmajor_desc(b);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                umma::mma_f16(tmem, ad + 2 * kk, bd + 2 * kk, idesc,
+                              (kb | kk) != 0);
+            if (SPLIT) {
+                const uint32_t a2 = b + S::B_BYTES, b2 = a2 + S::A_BYTES;
+                const uint64_t ad2 = umma::sw128_kmajor_desc(a2);
+                const uint64_t bd2 = umma::sw128_kmajor_desc(b2);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma::mma_f16(tmem + BN, ad + 2 * kk, bd2 + 2 * kk, idesc,
+                                  (kb | kk) != 0);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma::mma_f16(tmem + BN, ad2 + 2 * kk, bd + 2 * kk, idesc, 1);
+            }
+            umma::mma_commit(&empty[s]);
+        }
+        umma::mma_commit(&accum_bar);  // fires once every issued MMA is done
+    } else if (warp >= 2) {
+        // ----------------------------------------------------- epilogue
+        const int q = warp & 3;  // the 32-lane quarter of TMEM this warp reads
+        const int row = m0 + q * 32 + lane;
+        const bool ok = mbar_wait_bounded(&accum_bar, 0);
+        umma::fence_after_sync();
+        if (!ok) set_status(g.status, DEV_TIMEOUT);
+        if (ok && !abort_flag) {
+            const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
+            float *drow = g.D + (long long)row * g.ldd;
+            const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                umma::tmem_ld32(t_row + c, r);
+                float v[32];
+                if (SPLIT) {
+                    uint32_t r2[32];
+                    umma::tmem_ld32(t_row + BN + c, r2);
+                    umma::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        v[i] = fmaf(g.lo_scale, __uint_as_float(r2[i]),
+                                    __uint_as_float(r[i]));
+                } else {
+                    umma::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+                }
+                if (row < g.M) {
+                    const int col = n0 + c;
+                    if (vec && col + 32 <= g.N) {
+#pragma unroll
+                        for (int i = 0; i < 32; i += 4)
+                            *reinterpret_cast<float4 *>(drow + col + i) =
+                                make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (col + i < g.N) drow[col + i] = v[i];
+                    }
+                }
+            }
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, S::TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of a rows x inner matrix of 16-bit elements (row stride `ld`
+// elements), box = 64 elements x box_rows rows, 128-byte swizzle, zero fill.
+static bool make_map(CUtensorMap *m, const void *base, long long inner,
+                     long long rows, long long ld, int box_rows, bool bf16) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                    2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <int BN, bool SPLIT, int STAGES>
+static cudaError_t launch_gemm_t(const GemmOperands &op, unsigned *status,
+                                 cudaStream_t s) {
+    using S = GemmShape<BN, SPLIT, STAGES>;
+    CUtensorMap tA, tB, tA2, tB2;
+    if (!make_map(&tA, op.A_hi, op.K, op.M, op.lda, S::BM, op.bf16) ||
+        !make_map(&tB, op.B_hi, op.K, op.N, op.ldb, BN, op.bf16))
+        return cudaErrorInvalidValue;
+    if (SPLIT) {
+        if (!make_map(&tA2, op.A_lo, op.K, op.M, op.lda, S::BM, op.bf16) ||
+            !make_map(&tB2, op.B_lo, op.K, op.N, op.ldb, BN, op.bf16))
+            return cudaErrorInvalidValue;
+    } else {
+        tA2 = tA;
+        tB2 = tB;
+    }
+    auto kern = umma_gemm_kernel<BN, SPLIT, STAGES>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(
+            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status};
+    dim3 grid((op.N + BN - 1) / BN, (op.M + S::BM - 1) / S::BM);
+    const uint32_t idesc = umma::idesc_f16(S::BM, BN, op.bf16);
+    kern<<<grid, 192, S::SMEM, s>>>(tA, tB, tA2, tB2, g, idesc);
+    return cudaGetLastError();
+}
+
+bool gemm_operands_ok(const GemmOperands &op) {
+    if (op.M < 1 || op.N < 1 || op.K < 64 || op.K % 64) return false;
+    if (op.lda < op.K || op.ldb < op.K || op.lda % 8 || op.ldb % 8) return false;
+    if (op.ldd < op.N) return false;
+    auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    if (!al16(op.A_hi) || !al16(op.B_hi)) return false;
+    if (op.split && (!al16(op.A_lo) || !al16(op.B_lo))) return false;
+    if (((uintptr_t)op.D & 3) != 0) return false;
+    if (op.M > (1 << 30) || op.N > (1 << 30)) return false;
+    return true;
+}
+
+cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
+                             cudaStream_t s) {
+    if (!gemm_operands_ok(op)) return cudaErrorInvalidValue;
+    if (op.split) return launch_gemm_t<128, true, 3>(op, status, s);
+    return launch_gemm_t<128, false, 6>(op, status, s);
+}
+
+}  // namespace cgh
