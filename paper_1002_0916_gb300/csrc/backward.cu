@@ -1,0 +1,397 @@
+// backward.cu -- the hand-written adjoint of Eq. 1 (step A8).
+//
+// For a loss L with G = dL/dI (Ny x Nx) and phi = P_j r^2 (Section 1,
+// Eq. 1; P_j = 2 pi Q_j, dx = x - x_j, dy = y - y_j, dP_j/dz_j = -P_j/z_j):
+//     dL/dA_j = sum G cos(phi)
+//     dL/dx_j = 2 P_j A_j sum G sin(phi) dx
+//     dL/dy_j = 2 P_j A_j sum G sin(phi) dy
+//     dL/dz_j = (P_j A_j / z_j) sum G sin(phi) (dx^2 + dy^2)
+// Both methods produce per-tile partial sums
+//     part_x[t][j] = (sum G cos phi, sum G sin phi dx, sum G sin phi dx^2)
+//     part_y[t][j] = (-, sum G sin phi dy, sum G sin phi dy^2)
+// and one reduction kernel adds the tiles in a fixed order (deterministic)
+// and applies the per-point factors.
+//
+// Direct (FP32): each thread owns one point and walks a 16-pixel-wide
+// column strip of G top to bottom; G rows are read with uniform (broadcast)
+// loads; the x angles of the strip stay in registers and the y angle follows
+// the exact fixed-point form of the paper's Eq. 2 recurrence.  Two MUFU
+// operations (sin, cos) per point-pixel update.
+//
+// Separable (split FP16 on the tensor cores): with U = e^{i th_x},
+// V = e^{i th_y},
+//     sum_{x,y} G e^{i(th_x + th_y)} w(x) = sum_x w(x) U[x] (sum_y G[y][x] V[y])
+// so two GEMMs give the inner transforms -- D1[2j+c][x] = sum_y V'[2j+c][y] G[y][x]
+// and D2[2j+c][y] = sum_x U'[2j+c][x] G[y][x], with U', V' the cos/sin
+// rows -- and their epilogues (umma.cu) multiply by the recomputed U or V
+// and reduce over the GEMM columns with weights 1, d, d^2.  U and V are
+// recomputed from the point records here, not kept from the forward pass.
+// G is scaled by a power of two (from max |G|) before the FP16 split and
+// the scale is removed in the reduction.
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "api_internal.h"
+#include "common.cuh"
+
+namespace cgh {
+
+constexpr float ADJ_LO_SCALE = 4096.0f;
+
+// ------------------------------------------------------------- G prep
+__global__ void g_absmax_kernel(const float *__restrict__ G, long long n,
+                                unsigned *word) {
+    float m = 0.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float v = fabsf(G[i]);
+        m = v > m ? v : (v != v ? v : m);  // keep NaN
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        float t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : (t != t ? t : m);
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(word, __float_as_uint(m));
+}
+
+// 2^-e with e the exponent that maps max |G| into [1/2, 1); 1 if max is 0
+// or not finite.
+__device__ __forceinline__ float g_scale(unsigned word) {
+    const float m = __uint_as_float(word);
+    if (!(m > 0.0f) || !isfinite(m)) return 1.0f;
+    return ldexpf(1.0f, -(ilogbf(m) + 1));
+}
+
+// G (FP32, Ny x Nx) -> scaled FP16 hi/lo planes in both orientations:
+// Gr[y][x] (row stride ldx) and Gt[x][y] (row stride ldy).
+__global__ void g_convert_kernel(const float *__restrict__ G, int Nx, int Ny,
+                                 const unsigned *word, __half *Gr_hi,
+                                 __half *Gr_lo, int ldx, __half *Gt_hi,
+                                 __half *Gt_lo, int ldy) {
+    __shared__ float tile[32][33];
+    const float s = g_scale(*word);
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int y = by + r, x = bx + tx;
+        float v = 0.0f;
+        if (y < Ny && x < Nx) v = G[(size_t)y * Nx + x] * s;
+        tile[r][tx] = v;
+        if (y < Ny && x < Nx) {
+            const __half h = __float2half_rn(v);
+            Gr_hi[(size_t)y * ldx + x] = h;
+            Gr_lo[(size_t)y * ldx + x] =
+                __float2half_rn((v - __half2float(h)) * ADJ_LO_SCALE);
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int x = bx + r, y = by + tx;
+        if (x < Nx && y < Ny) {
+            const float v = tile[tx][r];
+            const __half h = __float2half_rn(v);
+            Gt_hi[(size_t)x * ldy + y] = h;
+            Gt_lo[(size_t)x * ldy + y] =
+                __float2half_rn((v - __half2float(h)) * ADJ_LO_SCALE);
+        }
+    }
+}
+
+// ---------------------------------------------------------- U', V' rows
+// Row 2j: cos th(u, j), row 2j+1: sin th(u, j), along u = 0..n-1, for the
+// x axis (U', n = Nx, row stride ldx) and the y axis (V', n = Ny, ldy).
+// FP16 hi and lo (scaled by 2^12) planes; rows of padding points are 0.
+__global__ void adj_tables_kernel(const PointRec *__restrict__ rec, int N,
+                                  int Npad, int Nx, int Ny, int ldx, int ldy,
+                                  __half *Uhi, __half *Ulo, __half *Vhi,
+                                  __half *Vlo) {
+    const long long total = (long long)Npad * (Nx + Ny);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / (Nx + Ny));
+        const int r = (int)(e - (long long)j * (Nx + Ny));
+        const bool is_x = r < Nx;
+        const int u = is_x ? r : r - Nx;
+        float s = 0.0f, c = 0.0f;
+        if (j < N) {
+            const PointRec pr = rec[j];
+            const uint64_t ph = is_x ? axis_phase(pr.c, pr.bx, pr.ax, u)
+                                     : axis_phase(pr.c, pr.by, pr.ay, u);
+            sincospif(2.0f * (float)phase_hi(ph) * TURN_PER_U32, &s, &c);
+        }
+        __half *hi = is_x ? Uhi : Vhi;
+        __half *lo = is_x ? Ulo : Vlo;
+        const int ld = is_x ? ldx : ldy;
+        const __half hc = __float2half_rn(c), hs = __float2half_rn(s);
+        const size_t oc = (size_t)(2 * j) * ld + u, os = oc + ld;
+        hi[oc] = hc;
+        hi[os] = hs;
+        lo[oc] = __float2half_rn((c - __half2float(hc)) * ADJ_LO_SCALE);
+        lo[os] = __float2half_rn((s - __half2float(hs)) * ADJ_LO_SCALE);
+    }
+}
+
+// ------------------------------------------------------ direct adjoint
+constexpr int BWD_STRIP = 16;    // pixels per column strip
+constexpr int BWD_THREADS = 128; // points per CTA
+
+__global__ void __launch_bounds__(BWD_THREADS)
+direct_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ points,
+                  int N, int Npad, int Nx, int Ny, const float *__restrict__ G,
+                  float *__restrict__ part_x, float *__restrict__ part_y) {
+    const int strip = blockIdx.x;
+    const int j = blockIdx.y * BWD_THREADS + threadIdx.x;
+    const int x0 = strip * BWD_STRIP;
+    const bool valid = j < N;
+    PointRec pr{};
+    float xj = 0.0f, yj = 0.0f;
+    if (valid) {
+        pr = rec[j];
+        xj = points[2 * j];
+        yj = points[2 * j + 1];
+    }
+    float tx[BWD_STRIP], dx[BWD_STRIP];
+#pragma unroll
+    for (int k = 0; k < BWD_STRIP; ++k) {
+        tx[k] = (float)phase_hi(axis_phase(pr.c, pr.bx, pr.ax, x0 + k)) * RAD_PER_U32;
+        dx[k] = (float)(x0 + k) - xj;
+    }
+    // y angle by the fixed-point recurrence: th(y+1) = th(y) + d(y),
+    // d(y+1) = d(y) + 2c (exact modulo one turn)
+    uint64_t th = pr.ay;
+    uint64_t dth = pr.c - pr.by;
+    const uint64_t d2 = 2 * pr.c;
+    const int ncols = Nx - x0 < BWD_STRIP ? Nx - x0 : BWD_STRIP;
+    const bool vec = (ncols == BWD_STRIP) && ((Nx & 3) == 0);
+    float sC = 0.0f, sX = 0.0f, sXX = 0.0f, sY = 0.0f, sYY = 0.0f;
+#pragma unroll 1
+    for (int y = 0; y < Ny; ++y) {
+        const float ty = (float)phase_hi(th) * RAD_PER_U32;
+        th += dth;
+        dth += d2;
+        const float dy = (float)y - yj;
+        const float *grow = G + (size_t)y * Nx + x0;
+        float g[BWD_STRIP];
+        if (vec) {
+#pragma unroll
+            for (int k = 0; k < BWD_STRIP; k += 4) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(grow + k));
+                g[k] = v.x;
+                g[k + 1] = v.y;
+                g[k + 2] = v.z;
+                g[k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < BWD_STRIP; ++k) g[k] = k < ncols ? __ldg(grow + k) : 0.0f;
+        }
+        float rs = 0.0f;
+#pragma unroll
+        for (int k = 0; k < BWD_STRIP; ++k) {
+            float s, c;
+            __sincosf(tx[k] + ty, &s, &c);
+            sC = fmaf(g[k], c, sC);
+            const float sg = g[k] * s;
+            const float t = sg * dx[k];
+            sX += t;
+            sXX = fmaf(t, dx[k], sXX);
+            rs += sg;
+        }
+        sY = fmaf(rs, dy, sY);
+        sYY = fmaf(rs * dy, dy, sYY);
+    }
+    if (valid) {
+        float *px = part_x + ((size_t)strip * Npad + j) * 3;
+        float *py = part_y + ((size_t)strip * Npad + j) * 3;
+        px[0] = sC;
+        px[1] = sX;
+        px[2] = sXX;
+        py[0] = 0.0f;
+        py[1] = sY;
+        py[2] = sYY;
+    }
+}
+
+// ------------------------------------------------------------ reduce
+__global__ void adjoint_reduce_kernel(const PointRec *__restrict__ rec,
+                                      const float *__restrict__ z, int N, int Npad,
+                                      const float *__restrict__ part_x, int Tx,
+                                      const float *__restrict__ part_y, int Ty,
+                                      const unsigned *gword, float *gpts, float *gA,
+                                      float *gz) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    double sC = 0, sX = 0, sXX = 0, sY = 0, sYY = 0;
+    for (int t = 0; t < Tx; ++t) {
+        const float *p = part_x + ((size_t)t * Npad + j) * 3;
+        sC += p[0];
+        sX += p[1];
+        sXX += p[2];
+    }
+    for (int t = 0; t < Ty; ++t) {
+        const float *p = part_y + ((size_t)t * Npad + j) * 3;
+        sY += p[1];
+        sYY += p[2];
+    }
+    const PointRec r = rec[j];
+    const bool ok = r.Q32 > 0.0f;
+    const double inv = gword ? 1.0 / (double)g_scale(*gword) : 1.0;
+    const double P = 6.283185307179586 * (double)r.Q32;
+    const double a = (double)r.A;
+    if (gA) gA[j] = ok ? (float)(sC * inv) : 0.0f;
+    if (gpts) {
+        gpts[2 * j] = ok ? (float)(2.0 * P * a * sX * inv) : 0.0f;
+        gpts[2 * j + 1] = ok ? (float)(2.0 * P * a * sY * inv) : 0.0f;
+    }
+    if (gz) gz[j] = ok ? (float)(P * a / (double)z[j] * (sXX + sYY) * inv) : 0.0f;
+}
+
+}  // namespace cgh
+
+using namespace cgh;
+
+static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
+                               const float *z, int N, double lambda, double p,
+                               int Nx, int Ny, const float *G, float *gpts,
+                               float *gA, float *gz, int method, cudaStream_t s) {
+    const bool sep = method == CGH_SEP_FP16X3;
+    const int Kp = pad_to(2 * N, 128);   // GEMM rows: whole 128-row tiles
+    const int Npad = sep ? Kp / 2 : pad_to(N, BWD_THREADS);
+    const int ldx = pad_to(Nx, 8), ldy = pad_to(Ny, 8);
+    const int Tx = sep ? (Nx + umma_tile_n() - 1) / umma_tile_n()
+                       : (Nx + BWD_STRIP - 1) / BWD_STRIP;
+    const int Ty = sep ? (Ny + umma_tile_n() - 1) / umma_tile_n() : Tx;
+    const size_t word_b = 256;
+    const size_t rec_b = align256((size_t)Npad * sizeof(PointRec));
+    const size_t px_b = align256((size_t)Tx * Npad * 3 * sizeof(float));
+    const size_t py_b = align256((size_t)Ty * Npad * 3 * sizeof(float));
+    size_t total = word_b + rec_b + px_b + py_b;
+    size_t u_b = 0, v_b = 0, gr_b = 0, gt_b = 0;
+    if (sep) {
+        u_b = align256((size_t)Kp * ldx * 2);
+        v_b = align256((size_t)Kp * ldy * 2);
+        gr_b = align256((size_t)Ny * ldx * 2);
+        gt_b = align256((size_t)Nx * ldy * 2);
+        total += 2 * (u_b + v_b + gr_b + gt_b);
+    }
+    cgh_status st = h->ensure(h->ws2, total, s, "adjoint workspace");
+    if (st) return st;
+    char *b = (char *)h->ws2.ptr;
+    unsigned *gword = (unsigned *)b;
+    PointRec *rec = (PointRec *)(b + word_b);
+    float *part_x = (float *)(b + word_b + rec_b);
+    float *part_y = (float *)(b + word_b + rec_b + px_b);
+    char *q = b + word_b + rec_b + px_b + py_b;
+
+    {
+        TimedLaunch tl(h, CGH_K_PROLOGUE, s);
+        cudaError_t e = launch_prologue(points, A, z, N, Npad, lambda, p, rec,
+                                        h->d_status, s);
+        if (e != cudaSuccess) return h->cuda_fail(e, "prologue launch");
+        tl.done();
+    }
+    if (!sep) {
+        TimedLaunch tl(h, CGH_K_BWD_DIRECT, s);
+        dim3 grid(Tx, Npad / BWD_THREADS);
+        direct_bwd_kernel<<<grid, BWD_THREADS, 0, s>>>(rec, points, N, Npad, Nx, Ny,
+                                                        G, part_x, part_y);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return h->cuda_fail(e, "direct adjoint launch");
+        tl.done();
+    } else {
+        __half *Uhi = (__half *)q, *Ulo = (__half *)(q + u_b);
+        __half *Vhi = (__half *)(q + 2 * u_b), *Vlo = (__half *)(q + 2 * u_b + v_b);
+        char *q2 = q + 2 * (u_b + v_b);
+        __half *Grh = (__half *)q2, *Grl = (__half *)(q2 + gr_b);
+        __half *Gth = (__half *)(q2 + 2 * gr_b), *Gtl = (__half *)(q2 + 2 * gr_b + gt_b);
+        cudaError_t e = cudaMemsetAsync(gword, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return h->cuda_fail(e, "cudaMemsetAsync");
+        {
+            TimedLaunch tl(h, CGH_K_AUX, s);
+            const long long n = (long long)Nx * Ny;
+            long long blocks = (n + 255) / 256;
+            if (blocks > 152 * 8) blocks = 152 * 8;
+            g_absmax_kernel<<<(int)blocks, 256, 0, s>>>(G, n, gword);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return h->cuda_fail(e, "G max launch");
+            tl.done();
+        }
+        {
+            TimedLaunch tl(h, CGH_K_AUX, s);
+            dim3 grid((Nx + 31) / 32, (Ny + 31) / 32);
+            g_convert_kernel<<<grid, dim3(32, 8), 0, s>>>(G, Nx, Ny, gword, Grh, Grl,
+                                                          ldx, Gth, Gtl, ldy);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return h->cuda_fail(e, "G convert launch");
+            tl.done();
+        }
+        {
+            TimedLaunch tl(h, CGH_K_SEP_TABLES, s);
+            const long long n = (long long)Npad * (Nx + Ny);
+            long long blocks = (n + 255) / 256;
+            if (blocks > 152 * 32) blocks = 152 * 32;
+            adj_tables_kernel<<<(int)blocks, 256, 0, s>>>(rec, N, Npad, Nx, Ny, ldx,
+                                                          ldy, Uhi, Ulo, Vhi, Vlo);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return h->cuda_fail(e, "adjoint tables launch");
+            tl.done();
+        }
+        // D1[k][x] = sum_y V'[k][y] G[y][x]: A = V' (Kp x Ny), B = G^T (Nx x Ny)
+        GemmOperands o1{};
+        o1.A_hi = Vhi; o1.A_lo = Vlo; o1.B_hi = Gth; o1.B_lo = Gtl;
+        o1.M = Kp; o1.N = Nx; o1.K = Ny; o1.lda = ldy; o1.ldb = ldy;
+        o1.bf16 = false; o1.split = true; o1.lo_scale = 1.0f / ADJ_LO_SCALE;
+        o1.D = nullptr; o1.ldd = Nx;
+        // D2[k][y] = sum_x U'[k][x] G[y][x]: A = U' (Kp x Nx), B = G (Ny x Nx)
+        GemmOperands o2 = o1;
+        o2.A_hi = Uhi; o2.A_lo = Ulo; o2.B_hi = Grh; o2.B_lo = Grl;
+        o2.M = Kp; o2.N = Ny; o2.K = Nx; o2.lda = ldx; o2.ldb = ldx; o2.ldd = Ny;
+        {
+            TimedLaunch tl(h, CGH_K_BWD_GEMM, s);
+            e = launch_umma_adjoint(o1, rec, points, N, Npad, 0, part_x, h->d_status, s);
+            if (e != cudaSuccess) return h->cuda_fail(e, "adjoint GEMM (x) launch");
+            tl.done();
+        }
+        {
+            TimedLaunch tl(h, CGH_K_BWD_GEMM, s);
+            e = launch_umma_adjoint(o2, rec, points, N, Npad, 1, part_y, h->d_status, s);
+            if (e != cudaSuccess) return h->cuda_fail(e, "adjoint GEMM (y) launch");
+            tl.done();
+        }
+    }
+    {
+        TimedLaunch tl(h, CGH_K_BWD_REDUCE, s);
+        adjoint_reduce_kernel<<<(N + 127) / 128, 128, 0, s>>>(
+            rec, z, N, Npad, part_x, Tx, part_y, Ty, sep ? gword : nullptr, gpts, gA,
+            gz);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return h->cuda_fail(e, "adjoint reduce launch");
+        tl.done();
+    }
+    return CGH_OK;
+}
+
+extern "C" cgh_status cgh_backward(cgh_handle h, const float *points,
+                                   const float *A, const float *z, int N,
+                                   double lambda, double p, int Nx, int Ny,
+                                   const float *grad_out, float *grad_points,
+                                   float *grad_A, float *grad_z, int method,
+                                   void *stream) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != h->device) cudaSetDevice(h->device);
+    h->err[0] = 0;
+    cgh_status st = h->check_problem(points, A, z, N, lambda, p, Nx, Ny, grad_out);
+    if (st == CGH_OK && method != CGH_DIRECT_FP32 && method != CGH_SEP_FP16X3)
+        st = h->fail(CGH_ERR_INVALID_ARG,
+                     "adjoint method must be CGH_DIRECT_FP32 or CGH_SEP_FP16X3");
+    if (st == CGH_OK &&
+        ((((uintptr_t)grad_points) | ((uintptr_t)grad_A) | ((uintptr_t)grad_z)) & 3))
+        st = h->fail(CGH_ERR_INVALID_ARG, "gradient arrays must be 4-byte aligned");
+    if (st == CGH_OK && N > 0 && (grad_points || grad_A || grad_z))
+        st = run_backward(h, points, A, z, N, lambda, p, Nx, Ny, grad_out,
+                          grad_points, grad_A, grad_z, method, (cudaStream_t)stream);
+    if (prev != h->device) cudaSetDevice(prev);
+    return st;
+}

@@ -170,6 +170,13 @@ struct GemmOperands {
 bool gemm_operands_ok(const GemmOperands &op);
 cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
                              cudaStream_t s);
+// Split GEMM whose epilogue reduces the adjoint sums over its columns into
+// part[n_tile][npad][3] (see umma.cu); rows are k = 2j + {0: cos, 1: sin}.
+cudaError_t launch_umma_adjoint(const GemmOperands &op, const PointRec *rec,
+                                const float *points, int npoints, int npad,
+                                int axis, float *part, unsigned *status,
+                                cudaStream_t s);
+int umma_tile_n();
 
 // separable.cu: U / V tables of the separable form.
 cudaError_t launch_sep_tables(const PointRec *rec, int N, int Npad, int Nx,

@@ -12,14 +12,6 @@ void cgh_ctx::release_all() {
 
 extern "C" {
 
-cgh_status cgh_backward(cgh_handle h, const float *, const float *,
-                        const float *, int, double, double, int, int,
-                        const float *, float *, float *, float *, int,
-                        void *) {
-    if (!h) return CGH_ERR_INVALID_ARG;
-    return h->fail(CGH_ERR_UNSUPPORTED, "adjoint not built yet");
-}
-
 cgh_status cgh_batch(cgh_handle h, const cgh_problem *, int, int, void *) {
     if (!h) return CGH_ERR_INVALID_ARG;
     return h->fail(CGH_ERR_UNSUPPORTED, "batch not built yet");

@@ -175,7 +175,7 @@ extern "C" cgh_status cgh_debug_gemm(cgh_handle h, const void *A, const void *B,
     op.lo_scale = 0.0f;
     op.D = D;
     op.ldd = N;
-    if (!A || !B || !D || !gemm_operands_ok(op))
+    if (!A || !B || !D || K % 64 != 0 || !gemm_operands_ok(op))
         return h->fail(CGH_ERR_INVALID_ARG,
                        "debug GEMM: need M, N >= 1, K a positive multiple of 64, "
                        "16-byte aligned A and B");

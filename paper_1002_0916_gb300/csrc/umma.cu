@@ -37,6 +37,23 @@ struct GemmArgs {
     unsigned *status;
 };
 
+// Fused adjoint epilogue (MODE 1).  The GEMM rows are k = 2j + c (c = 0:
+// cos row, 1: sin row of point j) and its columns are pixel coordinates u
+// along one image axis; D[2j][u] = W_c, D[2j+1][u] = W_s are the partial
+// transforms of dL/dI over the other axis.  With (cu, su) = (cos, sin) of
+// th_axis(u, j) and d = u - u_j the epilogue accumulates over its columns
+//     C = cu W_c - su W_s,   S = su W_c + cu W_s,
+//     part[tile][j] += (C, S d, S d^2)
+// (the pixel sums of G cos(phi), G sin(phi) d, G sin(phi) d^2).
+struct AdjEpiArgs {
+    const PointRec *rec;
+    const float *points;  // N x 2 (x_j, y_j)
+    int npoints;          // N
+    int npad;             // partial-sum stride (points)
+    int axis;             // 0: columns are x, 1: columns are y
+    float *part;          // [gridDim.x][npad][3]
+};
+
 template <int BN, bool SPLIT, int STAGES>
 struct GemmShape {
     static constexpr int BM = 128, BK = 64;
@@ -53,13 +70,83 @@ struct GemmShape {
     static_assert(SMEM <= 232448, "shared memory");
 };
 
-template <int BN, bool SPLIT, int STAGES>
+// The fused adjoint epilogue for one TMEM lane (= GEMM row `row`).
+template <int BN, bool SPLIT>
+__device__ __forceinline__ void adjoint_epilogue(uint32_t t_row, int row, int n0,
+                                                 const GemmArgs &g,
+                                                 const AdjEpiArgs &ea, int lane) {
+    const int j = row >> 1;
+    const bool cos_row = (row & 1) == 0;
+    const bool valid = j < ea.npoints;
+    PointRec pr{};
+    float uj = 0.0f;
+    if (valid) {
+        pr = ea.rec[j];
+        uj = ea.points[2 * j + ea.axis];
+    }
+    const uint64_t b = ea.axis == 0 ? pr.bx : pr.by;
+    const uint64_t a = ea.axis == 0 ? pr.ax : pr.ay;
+    // exact fixed-point phase at column n0 and its first difference
+    // (the paper's Eq. 2 recurrence, modulo one turn)
+    uint64_t th = axis_phase(pr.c, b, a, n0);
+    uint64_t dth = pr.c * (uint64_t)(2 * (long long)n0 + 1) - b;
+    const uint64_t d2 = 2 * pr.c;
+    float accC = 0.0f, accS1 = 0.0f, accS2 = 0.0f;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        umma::tmem_ld32(t_row + c, r);
+        float v[32];
+        if (SPLIT) {
+            uint32_t r2[32];
+            umma::tmem_ld32(t_row + BN + c, r2);
+            umma::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                v[i] = fmaf(g.lo_scale, __uint_as_float(r2[i]), __uint_as_float(r[i]));
+        } else {
+            umma::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+        }
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+            const float other = __shfl_xor_sync(0xffffffffu, v[i], 1);
+            const float wc = cos_row ? v[i] : other;
+            const float ws = cos_row ? other : v[i];
+            const float ang = (float)phase_hi(th) * RAD_PER_U32;
+            th += dth;
+            dth += d2;
+            float su, cu;
+            __sincosf(ang, &su, &cu);
+            const int u = n0 + c + i;
+            const float d = (float)u - uj;
+            const float C = cu * wc - su * ws;
+            const float Sv = su * wc + cu * ws;
+            if (u < g.N) {
+                accC += C;
+                const float t = Sv * d;
+                accS1 += t;
+                accS2 = fmaf(t, d, accS2);
+            }
+        }
+    }
+    if (valid && cos_row) {
+        float *p = ea.part + ((size_t)blockIdx.x * ea.npad + j) * 3;
+        p[0] = accC;
+        p[1] = accS1;
+        p[2] = accS2;
+    }
+    (void)lane;
+}
+
+template <int BN, bool SPLIT, int STAGES, int MODE>
 __global__ void __launch_bounds__(192, 1)
 umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
                  const __grid_constant__ CUtensorMap tB,
                  const __grid_constant__ CUtensorMap tA2,
                  const __grid_constant__ CUtensorMap tB2, GemmArgs g,
-                 uint32_t idesc) {
+                 AdjEpiArgs ea, uint32_t idesc) {
     using S = GemmShape<BN, SPLIT, STAGES>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[STAGES];
@@ -71,7 +158,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = blockIdx.x * BN, m0 = blockIdx.y * S::BM;
-    const int KB = g.K / S::BK;
+    const int KB = (g.K + S::BK - 1) / S::BK;
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -162,10 +249,15 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
         // ----------------------------------------------------- epilogue
         const int q = warp & 3;  // the 32-lane quarter of TMEM this warp reads
         const int row = m0 + q * 32 + lane;
-        const bool ok = mbar_wait_bounded(&accum_bar, 0);
+        // warp-uniform, so the .sync.aligned TMEM loads and the shuffles
+        // below are executed by whole warps
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accum_bar, 0));
         umma::fence_after_sync();
         if (!ok) set_status(g.status, DEV_TIMEOUT);
-        if (ok && !abort_flag) {
+        if (MODE == 1 && ok && !abort_flag) {
+            adjoint_epilogue<BN, SPLIT>(tmem + ((uint32_t)(q * 32) << 16), row, n0,
+                                        g, ea, lane);
+        } else if (ok && !abort_flag) {
             const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
             float *drow = g.D + (long long)row * g.ldd;
             const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
@@ -246,9 +338,9 @@ static bool make_map(CUtensorMap *m, const void *base, long long inner,
     return r == CUDA_SUCCESS;
 }
 
-template <int BN, bool SPLIT, int STAGES>
-static cudaError_t launch_gemm_t(const GemmOperands &op, unsigned *status,
-                                 cudaStream_t s) {
+template <int BN, bool SPLIT, int STAGES, int MODE>
+static cudaError_t launch_gemm_t(const GemmOperands &op, const AdjEpiArgs &ea,
+                                 unsigned *status, cudaStream_t s) {
     using S = GemmShape<BN, SPLIT, STAGES>;
     CUtensorMap tA, tB, tA2, tB2;
     if (!make_map(&tA, op.A_hi, op.K, op.M, op.lda, S::BM, op.bf16) ||
@@ -262,7 +354,7 @@ static cudaError_t launch_gemm_t(const GemmOperands &op, unsigned *status,
         tA2 = tA;
         tB2 = tB;
     }
-    auto kern = umma_gemm_kernel<BN, SPLIT, STAGES>;
+    auto kern = umma_gemm_kernel<BN, SPLIT, STAGES, MODE>;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -275,12 +367,12 @@ static cudaError_t launch_gemm_t(const GemmOperands &op, unsigned *status,
     GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status};
     dim3 grid((op.N + BN - 1) / BN, (op.M + S::BM - 1) / S::BM);
     const uint32_t idesc = umma::idesc_f16(S::BM, BN, op.bf16);
-    kern<<<grid, 192, S::SMEM, s>>>(tA, tB, tA2, tB2, g, idesc);
+    kern<<<grid, 192, S::SMEM, s>>>(tA, tB, tA2, tB2, g, ea, idesc);
     return cudaGetLastError();
 }
 
 bool gemm_operands_ok(const GemmOperands &op) {
-    if (op.M < 1 || op.N < 1 || op.K < 64 || op.K % 64) return false;
+    if (op.M < 1 || op.N < 1 || op.K < 1) return false;
     if (op.lda < op.K || op.ldb < op.K || op.lda % 8 || op.ldb % 8) return false;
     if (op.ldd < op.N) return false;
     auto al16 = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
@@ -294,8 +386,20 @@ bool gemm_operands_ok(const GemmOperands &op) {
 cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
                              cudaStream_t s) {
     if (!gemm_operands_ok(op)) return cudaErrorInvalidValue;
-    if (op.split) return launch_gemm_t<128, true, 3>(op, status, s);
-    return launch_gemm_t<128, false, 6>(op, status, s);
+    AdjEpiArgs ea{};
+    if (op.split) return launch_gemm_t<128, true, 3, 0>(op, ea, status, s);
+    return launch_gemm_t<128, false, 6, 0>(op, ea, status, s);
 }
+
+cudaError_t launch_umma_adjoint(const GemmOperands &op, const PointRec *rec,
+                                const float *points, int npoints, int npad,
+                                int axis, float *part, unsigned *status,
+                                cudaStream_t s) {
+    if (!gemm_operands_ok(op) || !op.split || (op.M & 1)) return cudaErrorInvalidValue;
+    AdjEpiArgs ea{rec, points, npoints, npad, axis, part};
+    return launch_gemm_t<128, true, 3, 1>(op, ea, status, s);
+}
+
+int umma_tile_n() { return 128; }
 
 }  // namespace cgh
