@@ -141,9 +141,14 @@ typedef struct {
  * (after one prologue launch).  probs: host array of `count` problems
  * (1 <= count <= 4096).  The work list of (problem, tile) items is built on
  * the host, sorted longest-first, and pulled by the persistent CTAs from an
- * atomic counter.  method: CGH_DIRECT_FP32 or CGH_SEP_FP16X3.  The call may
- * be captured into a CUDA graph once an uncaptured call of the same batch
- * geometry has sized the workspace.  Errors as cgh_forward. */
+ * atomic counter.  method: CGH_DIRECT_FP32 or CGH_SEP_FP16X3.
+ * The launches are captured once per batch geometry (problem count, sizes,
+ * constants and buffer addresses) into a CUDA graph that later calls of the
+ * same geometry replay; the graph reads the buffers' current contents.
+ * The call may itself be captured into a caller's graph once an uncaptured
+ * call of the same geometry has run (else CGH_ERR_UNSUPPORTED); such a
+ * captured graph stays valid until the handle runs a batch of another
+ * geometry.  Errors as cgh_forward; an argument error names the problem. */
 cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int count,
                      int method, void *stream);
 
@@ -184,7 +189,7 @@ cgh_status cgh_forward_noalloc(const float *points, const float *A,
                                const float *z, int N, double lambda, double p,
                                int Nx, int Ny, float *out, void *stream);
 
-/* Tile shape of the direct kernel. */
+/* Tile shape of the direct kernel (also used by the persistent batch). */
 typedef struct {
     int tile_x;            /* pixels per CTA along x           */
     int tile_y;            /* pixels per CTA along y           */
@@ -237,6 +242,13 @@ cgh_status cgh_kernel_timing(cgh_handle h, int enable);
  * recorded events. */
 cgh_status cgh_kernel_time(cgh_handle h, int kernel, double *total_ms,
                            uint64_t *launches);
+
+/* Autotuner for cgh_batch with CGH_DIRECT_FP32: time every compiled tile
+ * shape on this batch (its geometry and data; synchronises `stream`), keep
+ * the fastest for batches of the same sizes, write it to *chosen (may be
+ * NULL).  Errors as cgh_batch; CGH_ERR_UNSUPPORTED for other methods. */
+cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs, int count,
+                          int method, void *stream, cgh_direct_tile *chosen);
 
 /* Synchronise `stream`, then read and clear the handle's device status
  * word: CGH_OK, CGH_ERR_INVALID_ARG (a point had z <= 0 or a non-finite

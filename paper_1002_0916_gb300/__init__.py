@@ -27,7 +27,7 @@ __all__ = [
     "cgh_set_direct_tile", "cgh_direct_tiles", "cgh_last_device_status",
     "cgh_launch_count", "cgh_status_string", "cgh_last_error",
     "cgh_debug_gemm", "CGHFunction", "default_handle", "KERNELS",
-    "cgh_kernel_timing", "cgh_kernel_time",
+    "cgh_kernel_timing", "cgh_kernel_time", "cgh_tune_batch",
 ]
 
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
@@ -81,6 +81,9 @@ def _load():
     L.cgh_direct_tile_get.argtypes = [ci, ctypes.POINTER(_Tile)]
     L.cgh_set_direct_tile.argtypes = [vp, ctypes.POINTER(_Tile)]
     L.cgh_tune.argtypes = [vp, ci, ci, ci, ci, vp, ctypes.POINTER(_Tile)]
+    L.cgh_tune_batch.argtypes = [vp, ctypes.POINTER(_Problem), ci, ci, vp,
+                                 ctypes.POINTER(_Tile)]
+    L.cgh_tune_batch.restype = ci
     L.cgh_last_device_status.argtypes = [vp, vp]
     L.cgh_launch_count.argtypes = [vp]
     L.cgh_launch_count.restype = ctypes.c_uint64
@@ -265,10 +268,7 @@ def cgh_backward(points, A, z, lam: float, p: float, Nx: int, Ny: int,
 
 
 # --------------------------------------------------------------- batch
-def cgh_batch(problems: Sequence[dict], *, method="direct", handle=None,
-              stream=None):
-    """Many holograms in one persistent launch.  Each problem is a dict with
-    points, A, z (CUDA tensors), lam, p, Nx, Ny and out (CUDA tensor)."""
+def _problems(problems):
     n = len(problems)
     arr = (_Problem * max(n, 1))()
     for i, pr in enumerate(problems):
@@ -282,10 +282,28 @@ def cgh_batch(problems: Sequence[dict], *, method="direct", handle=None,
         arr[i].Nx = int(pr["Nx"])
         arr[i].Ny = int(pr["Ny"])
         arr[i].out = _dev_f32(pr["out"], "out", int(pr["Nx"]) * int(pr["Ny"]))
+    return arr, n
+
+
+def cgh_batch(problems: Sequence[dict], *, method="direct", handle=None,
+              stream=None):
+    """Many holograms in one persistent launch.  Each problem is a dict with
+    points, A, z (CUDA tensors), lam, p, Nx, Ny and out (CUDA tensor)."""
+    arr, n = _problems(problems)
     dev = problems[0]["A"].device.index if n else None
     h = handle if handle is not None else default_handle(dev)
     st = _L().cgh_batch(h, arr, n, _method(method), _stream_ptr(stream))
     _check(h, st, "cgh_batch")
+
+
+def cgh_tune_batch(h, problems: Sequence[dict], method="direct", stream=None):
+    """Time every direct tile shape on this batch; returns the fastest."""
+    arr, n = _problems(problems)
+    t = _Tile()
+    st = _L().cgh_tune_batch(h, arr, n, _method(method), _stream_ptr(stream),
+                             ctypes.byref(t))
+    _check(h, st, "cgh_tune_batch")
+    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage)
 
 
 # ---------------------------------------------------------- tiles/tuning

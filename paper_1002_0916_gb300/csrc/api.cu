@@ -199,6 +199,25 @@ cgh_status cgh_ctx::forward(const float *points, const float *A,
     }
 }
 
+// ------------------------------------------------------------- release
+void cgh_ctx::release_all() {
+    for (Buffer *b : {&ws, &ws2, &io, &part, &meta, &bws}) {
+        if (b->ptr) cudaFree(b->ptr);
+        b->ptr = nullptr;
+        b->bytes = 0;
+    }
+    if (batch_exec) cudaGraphExecDestroy(batch_exec);
+    batch_exec = nullptr;
+    batch_key = 0;
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    cap_stream = nullptr;
+    if (stage_done) cudaEventDestroy(stage_done);
+    stage_done = nullptr;
+    if (host_stage) cudaFreeHost(host_stage);
+    host_stage = nullptr;
+    host_stage_bytes = 0;
+}
+
 // --------------------------------------------------------- kernel timing
 cudaEvent_t cgh_ctx::get_event() {
     if (!event_pool.empty()) {

@@ -5,6 +5,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <unordered_map>
 #include <utility>
@@ -36,6 +37,16 @@ struct cgh_ctx {
     Buffer io;    // staging for cgh_forward_host
     Buffer part;  // partial sums of the adjoint
     Buffer meta;  // small per-call metadata (tensor maps, work lists)
+    Buffer bws;   // batch workspace: per-problem records and tables
+
+    // batch: pinned staging of the work list, a private capture stream and
+    // the instantiated graph of the last batch geometry
+    void *host_stage = nullptr;
+    size_t host_stage_bytes = 0;
+    cudaEvent_t stage_done = nullptr;  // last copy out of host_stage
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t batch_exec = nullptr;
+    uint64_t batch_key = 0;
 
     // kernel timing (cgh_kernel_timing / cgh_kernel_time)
     bool timing = false;
@@ -75,12 +86,26 @@ struct cgh_ctx {
                                  int Nx, int Ny, float *out, int method,
                                  cudaStream_t s);
 
+    cgh_status batch(const cgh_problem *probs, int count, int method,
+                     cudaStream_t s, int forced_tile_index);
+    cgh_status batch_direct(const cgh_problem *probs, int count, cudaStream_t s,
+                            int tile_index);
+    cgh_status batch_separable(const cgh_problem *probs, int count,
+                               cudaStream_t s);
+    cgh_status ensure_host_stage(size_t bytes);
+    cgh_status run_batch_graph(uint64_t key, size_t meta_b, int nkernels,
+                               const std::function<void(char *)> &fill_stage,
+                               const std::function<cudaError_t(cudaStream_t)> &enqueue,
+                               cudaStream_t s);
+
     void load_tune_cache();
     void release_all();
 };
 
 // autotune.cu
 std::string size_bucket(int method, int N, int Nx, int Ny);
+// batch.cu: tuning-cache key of a batch geometry (sizes only)
+std::string batch_bucket(const cgh_problem *probs, int count);
 int default_direct_tile(int N, int Nx, int Ny, int sm_count);
 
 // Brackets one kernel launch with events when the handle's timing is on,

@@ -1,0 +1,217 @@
+// direct_tile.cuh -- the staged point loop of the direct kernel for one
+// pixel tile, shared by the single-hologram kernel (direct.cu) and the
+// persistent batch kernel (batch.cu).  Internal to libcgh.
+#pragma once
+
+#include "common.cuh"
+
+namespace cgh {
+
+// The tile shapes compiled in: X(TX, TY, VX, VY, PT, NST) = pixels per CTA
+// along x and y, pixels per thread along x and y, points per shared-memory
+// stage, stages.  Every shape has 256 threads per CTA.
+#define CGH_DIRECT_TILES(X)          \
+    X(64, 64, 4, 4, 32, 3)           \
+    X(64, 32, 4, 2, 32, 3)           \
+    X(128, 32, 4, 4, 32, 3)          \
+    X(32, 32, 2, 2, 64, 3)           \
+    X(128, 64, 8, 4, 16, 3)          \
+    X(64, 16, 4, 1, 64, 3)
+
+// ------------------------------------------------------------- tables
+// Entries of the per-axis angle tables of one problem: x angles laid out
+// [x tile][point][x in tile], then y angles [y tile][point][y in tile], then
+// the amplitudes [point].
+__device__ __forceinline__ long long direct_table_entries(int Npad, int TX,
+                                                          int TY, int nxt,
+                                                          int nyt) {
+    return (long long)nxt * Npad * TX + (long long)nyt * Npad * TY + Npad;
+}
+
+__device__ __forceinline__ void direct_table_entry(
+    const PointRec *__restrict__ rec, int Npad, int TX, int TY, int nxt,
+    int nyt, long long e, float *__restrict__ phx, float *__restrict__ phy,
+    float *__restrict__ amp) {
+    const long long nx_e = (long long)nxt * Npad * TX;
+    const long long ny_e = (long long)nyt * Npad * TY;
+    if (e < nx_e) {
+        long long per = (long long)Npad * TX;
+        int t = (int)(e / per);
+        long long rem = e - (long long)t * per;
+        int j = (int)(rem / TX);
+        int i = (int)(rem - (long long)j * TX);
+        const PointRec &r = rec[j];
+        uint64_t ph = axis_phase(r.c, r.bx, r.ax, t * TX + i);
+        phx[e] = (float)phase_hi(ph) * RAD_PER_U32;
+    } else if (e < nx_e + ny_e) {
+        long long f = e - nx_e;
+        long long per = (long long)Npad * TY;
+        int t = (int)(f / per);
+        long long rem = f - (long long)t * per;
+        int j = (int)(rem / TY);
+        int i = (int)(rem - (long long)j * TY);
+        const PointRec &r = rec[j];
+        uint64_t ph = axis_phase(r.c, r.by, r.ay, t * TY + i);
+        phy[f] = (float)phase_hi(ph) * RAD_PER_U32;
+    } else {
+        int j = (int)(e - nx_e - ny_e);
+        amp[j] = rec[j].A;
+    }
+}
+
+template <int N>
+struct VecLoad;
+template <>
+struct VecLoad<1> {
+    __device__ static void ld(float *v, const float *p) { v[0] = p[0]; }
+};
+template <>
+struct VecLoad<2> {
+    __device__ static void ld(float *v, const float *p) {
+        float2 t = *reinterpret_cast<const float2 *>(p);
+        v[0] = t.x;
+        v[1] = t.y;
+    }
+};
+template <>
+struct VecLoad<4> {
+    __device__ static void ld(float *v, const float *p) {
+        float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    }
+};
+template <>
+struct VecLoad<8> {
+    __device__ static void ld(float *v, const float *p) {
+        VecLoad<4>::ld(v, p);
+        VecLoad<4>::ld(v + 4, p + 4);
+    }
+};
+
+template <int TX, int TY, int VX, int VY, int PT, int NST>
+struct DirectShape {
+    static constexpr int NTX = TX / VX;
+    static constexpr int THREADS = NTX * (TY / VY);
+    static constexpr int SX = PT * TX;        // floats of x-angles per stage
+    static constexpr int SY = PT * TY;        // floats of y-angles per stage
+    static constexpr int SA = PT;             // amplitudes per stage
+    static constexpr int STAGE = SX + SY + SA;
+    static constexpr size_t SMEM = (size_t)NST * STAGE * sizeof(float);
+    static_assert(TX % VX == 0 && TY % VY == 0, "tile not divisible");
+    static_assert(PT % 4 == 0, "bulk copies need 16-byte multiples");
+    static_assert((STAGE * 4) % 16 == 0, "stage alignment");
+};
+
+
+// Per-CTA driver of the staged loop.  Point tile t of a pixel tile is the
+// (g0 + t)-th stage load of the CTA, so a persistent CTA can run many pixel
+// tiles back to back on the same NST-slot ring and mbarriers: slot
+// (g0 + t) % NST, barrier parity ((g0 + t) / NST) & 1.
+template <int TX, int TY, int VX, int VY, int PT, int NST>
+struct DirectTileLoop {
+    using S = DirectShape<TX, TY, VX, VY, PT, NST>;
+
+    __device__ static void issue(float *smem, uint64_t *full, const float *gx,
+                                 const float *gy, const float *amp, int t,
+                                 int slot) {
+        float *st = smem + slot * S::STAGE;
+        mbar_arrive_expect_tx(&full[slot], S::STAGE * 4);
+        bulk_g2s(st, gx + (size_t)t * S::SX, S::SX * 4, &full[slot]);
+        bulk_g2s(st + S::SX, gy + (size_t)t * S::SY, S::SY * 4, &full[slot]);
+        bulk_g2s(st + S::SX + S::SY, amp + (size_t)t * S::SA, S::SA * 4,
+                 &full[slot]);
+    }
+
+    // acc += the point tiles [0, ntile) for this thread's VX x VY pixels.
+    // Returns false (after letting its own copies land) if a wait timed out.
+    __device__ static bool accumulate(float *smem, uint64_t *full,
+                                      volatile int *abort_flag, const float *gx,
+                                      const float *gy, const float *amp,
+                                      int ntile, unsigned g0,
+                                      float (&acc)[VY][VX], unsigned *status) {
+        int issued = 0;  // meaningful in thread 0 only
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < NST && s < ntile; ++s) {
+                issue(smem, full, gx, gy, amp, s, (int)((g0 + s) % NST));
+                ++issued;
+            }
+        }
+        const int tx = threadIdx.x % S::NTX, ty = threadIdx.x / S::NTX;
+        int t = 0;
+        for (; t < ntile; ++t) {
+            const unsigned g = g0 + (unsigned)t;
+            const int s = (int)(g % NST);
+            const uint32_t par = (uint32_t)((g / NST) & 1);
+            bool ok = mbar_wait_bounded(&full[s], par);
+            if (!ok) {
+                *abort_flag = 1;
+                set_status(status, DEV_TIMEOUT);
+            } else {
+                const float *st = smem + s * S::STAGE;
+                const float *sx = st + tx * VX;
+                const float *sy = st + S::SX + ty * VY;
+                const float *sa = st + S::SX + S::SY;
+#pragma unroll 2
+                for (int q = 0; q < PT; ++q) {
+                    const float a = sa[q];
+                    float vx[VX], vy[VY];
+                    VecLoad<VX>::ld(vx, sx + q * TX);
+                    VecLoad<VY>::ld(vy, sy + q * TY);
+#pragma unroll
+                    for (int i = 0; i < VY; ++i)
+#pragma unroll
+                        for (int k = 0; k < VX; ++k)
+                            acc[i][k] = fmaf(a, __cosf(vx[k] + vy[i]), acc[i][k]);
+                }
+            }
+            __syncthreads();  // every thread is done with slot s
+            if (*abort_flag) break;
+            if (threadIdx.x == 0 && t + NST < ntile) {
+                fence_proxy_async_smem();
+                issue(smem, full, gx, gy, amp, t + NST, s);
+                ++issued;
+            }
+        }
+        if (*abort_flag) {
+            // let the copies still in flight land before the shared memory
+            // goes away (each wait bounded again)
+            if (threadIdx.x == 0) {
+                for (int u = t; u < issued; ++u) {
+                    const unsigned g = g0 + (unsigned)u;
+                    mbar_wait_bounded(&full[g % NST], (uint32_t)((g / NST) & 1));
+                }
+            }
+            return false;
+        }
+        return true;
+    }
+
+    // Store the VX x VY pixels of this thread (pixel tile xt, yt).
+    __device__ static void store(const float (&acc)[VY][VX], int xt, int yt,
+                                 int Nx, int Ny, float *out, int vec_store) {
+        const int tx = threadIdx.x % S::NTX, ty = threadIdx.x / S::NTX;
+        const int x0 = xt * TX + tx * VX, y0 = yt * TY + ty * VY;
+#pragma unroll
+        for (int i = 0; i < VY; ++i) {
+            const int y = y0 + i;
+            if (y >= Ny) break;
+            float *orow = out + (size_t)y * Nx;
+            if (VX % 4 == 0 && vec_store && x0 + VX <= Nx) {
+#pragma unroll
+                for (int k = 0; k < VX; k += 4)
+                    *reinterpret_cast<float4 *>(orow + x0 + k) =
+                        make_float4(acc[i][k], acc[i][k + 1], acc[i][k + 2],
+                                    acc[i][k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < VX; ++k)
+                    if (x0 + k < Nx) orow[x0 + k] = acc[i][k];
+            }
+        }
+    }
+};
+
+}  // namespace cgh

@@ -402,4 +402,232 @@ cudaError_t launch_umma_adjoint(const GemmOperands &op, const PointRec *rec,
 
 int umma_tile_n() { return 128; }
 
+// ------------------------------------------------------ grouped (batch)
+// Persistent grouped split GEMM: work items (problem, m tile, n tile) are
+// taken round-robin by the CTAs (one per SM) in the order of a host list
+// sorted longest-K first.  The producer and MMA roles run ahead across
+// items; two TMEM accumulator buffers let the epilogue of item i overlap
+// the main loop of item i + 1 (acc_full / acc_empty mbarriers).
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+umma_grouped_kernel(const GroupProb *__restrict__ probs,
+                    const uint2 *__restrict__ items, int nitems,
+                    unsigned *status) {
+    using S = GemmShape<BN, true, STAGES>;
+    constexpr uint32_t ACC_COLS = 2 * BN;          // hi*hi and cross terms
+    constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;   // two buffers
+    static_assert(TMEM_COLS <= 512, "TMEM");
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[STAGES];
+    __shared__ __align__(8) uint64_t empty[STAGES];
+    __shared__ __align__(8) uint64_t acc_full[2];
+    __shared__ __align__(8) uint64_t acc_empty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+        }
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        umma::tmem_alloc(&tmem_base, TMEM_COLS);
+        umma::tmem_relinquish();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------- producer
+        unsigned g = 0, issued_from = 0;
+        for (int it = blockIdx.x; it < nitems && !abort_flag; it += gridDim.x) {
+            const uint2 w = items[it];
+            const GroupProb *gp = probs + w.x;
+            const int m0 = (int)(w.y & 0xffffu) * S::BM, n0 = (int)(w.y >> 16) * BN;
+            const int KB = (gp->K + S::BK - 1) / S::BK;
+            for (int kb = 0; kb < KB; ++kb, ++g) {
+                const int s = (int)(g % STAGES);
+                if (g >= STAGES &&
+                    !mbar_wait_bounded(&empty[s], (uint32_t)(((g / STAGES) - 1) & 1))) {
+                    abort_flag = 1;
+                    set_status(status, DEV_TIMEOUT);
+                }
+                if (abort_flag) break;
+                uint8_t *st = smem + (size_t)s * S::STAGE_BYTES;
+                mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
+                umma::tma_load_2d(st, &gp->tA, kb * S::BK, m0, &full[s]);
+                umma::tma_load_2d(st + S::A_BYTES, &gp->tB, kb * S::BK, n0, &full[s]);
+                umma::tma_load_2d(st + S::A_BYTES + S::B_BYTES, &gp->tA2, kb * S::BK,
+                                  m0, &full[s]);
+                umma::tma_load_2d(st + 2 * S::A_BYTES + S::B_BYTES, &gp->tB2,
+                                  kb * S::BK, n0, &full[s]);
+                issued_from = g + 1;
+            }
+        }
+        if (abort_flag) {
+            unsigned lo = issued_from > STAGES ? issued_from - STAGES : 0;
+            for (unsigned u = lo; u < issued_from; ++u)
+                mbar_wait_bounded(&full[u % STAGES], (uint32_t)((u / STAGES) & 1));
+        }
+    } else if (warp == 1 && lane == 0) {
+        // --------------------------------------------------- MMA issuer
+        const uint32_t idesc = umma::idesc_f16(S::BM, BN, false);
+        unsigned g = 0;
+        int n = 0;
+        for (int it = blockIdx.x; it < nitems && !abort_flag; it += gridDim.x, ++n) {
+            const int b = n & 1;
+            if (!mbar_wait_bounded(&acc_empty[b], (uint32_t)(((n >> 1) & 1) ^ 1))) {
+                abort_flag = 1;
+                set_status(status, DEV_TIMEOUT);
+                break;
+            }
+            umma::fence_after_sync();
+            const uint32_t d0 = tmem + (uint32_t)b * ACC_COLS, d1 = d0 + BN;
+            const GroupProb *gp = probs + items[it].x;
+            const int KB = (gp->K + S::BK - 1) / S::BK;
+            for (int kb = 0; kb < KB; ++kb, ++g) {
+                const int s = (int)(g % STAGES);
+                if (!mbar_wait_bounded(&full[s], (uint32_t)((g / STAGES) & 1))) {
+                    abort_flag = 1;
+                    set_status(status, DEV_TIMEOUT);
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint32_t a = smem_u32(smem + (size_t)s * S::STAGE_BYTES);
+                const uint32_t bb = a + S::A_BYTES;
+                const uint32_t a2 = bb + S::B_BYTES, b2 = a2 + S::A_BYTES;
+                const uint64_t ad = umma::sw128_kmajor_desc(a);
+                const uint64_t bd = umma::sw128_kmajor_desc(bb);
+                const uint64_t ad2 = umma::sw128_kmajor_desc(a2);
+                const uint64_t bd2 = umma::sw128_kmajor_desc(b2);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma::mma_f16(d0, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma::mma_f16(d1, ad + 2 * kk, bd2 + 2 * kk, idesc, (kb | kk) != 0);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma::mma_f16(d1, ad2 + 2 * kk, bd + 2 * kk, idesc, 1);
+                umma::mma_commit(&empty[s]);
+            }
+            umma::mma_commit(&acc_full[b]);
+        }
+    } else if (warp >= 2) {
+        // ----------------------------------------------------- epilogue
+        const int q = warp & 3;
+        int n = 0;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++n) {
+            const int b = n & 1;
+            const bool ok = __all_sync(
+                0xffffffffu, mbar_wait_bounded(&acc_full[b], (uint32_t)((n >> 1) & 1)));
+            umma::fence_after_sync();
+            if (!ok || abort_flag) {
+                if (!ok) set_status(status, DEV_TIMEOUT);
+                break;
+            }
+            const uint2 w = items[it];
+            const GroupProb *gp = probs + w.x;
+            const int m0 = (int)(w.y & 0xffffu) * S::BM, n0 = (int)(w.y >> 16) * BN;
+            const int row = m0 + q * 32 + lane;
+            const int M = gp->M, Ncols = gp->N;
+            const long long ldd = gp->ldd;
+            const float los = gp->lo_scale;
+            float *drow = gp->D + (long long)row * ldd;
+            const bool vec = ((ldd & 3) == 0) && ((((uintptr_t)gp->D) & 15) == 0);
+            const uint32_t t_row =
+                tmem + (uint32_t)b * ACC_COLS + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32], r2[32];
+                umma::tmem_ld32(t_row + c, r);
+                umma::tmem_ld32(t_row + BN + c, r2);
+                umma::tmem_ld_wait();
+                float v[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    v[i] = fmaf(los, __uint_as_float(r2[i]), __uint_as_float(r[i]));
+                if (row < M) {
+                    const int col = n0 + c;
+                    if (vec && col + 32 <= Ncols) {
+#pragma unroll
+                        for (int i = 0; i < 32; i += 4)
+                            *reinterpret_cast<float4 *>(drow + col + i) =
+                                make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (col + i < Ncols) drow[col + i] = v[i];
+                    }
+                }
+            }
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        umma::fence_after_sync();
+        umma::tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+constexpr int GROUP_BN = 128, GROUP_STAGES = 3;
+
+bool encode_group_prob(GroupProb *gp, const GemmOperands &op) {
+    if (!gemm_operands_ok(op) || !op.split) return false;
+    if (!make_map(&gp->tA, op.A_hi, op.K, op.M, op.lda, 128, op.bf16) ||
+        !make_map(&gp->tB, op.B_hi, op.K, op.N, op.ldb, GROUP_BN, op.bf16) ||
+        !make_map(&gp->tA2, op.A_lo, op.K, op.M, op.lda, 128, op.bf16) ||
+        !make_map(&gp->tB2, op.B_lo, op.K, op.N, op.ldb, GROUP_BN, op.bf16))
+        return false;
+    gp->D = op.D;
+    gp->ldd = op.ldd;
+    gp->M = op.M;
+    gp->N = op.N;
+    gp->K = op.K;
+    gp->lo_scale = op.lo_scale;
+    return true;
+}
+
+cudaError_t prepare_umma_grouped() {
+    using S = GemmShape<GROUP_BN, true, GROUP_STAGES>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(umma_grouped_kernel<GROUP_BN, GROUP_STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::SMEM);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
+    return e;
+}
+
+cudaError_t launch_umma_grouped(const GroupProb *probs, const uint2 *items,
+                                int nitems, unsigned *status, int sm_count,
+                                cudaStream_t s) {
+    using S = GemmShape<GROUP_BN, true, GROUP_STAGES>;
+    if (nitems <= 0) return cudaSuccess;
+    int grid = nitems < sm_count ? nitems : sm_count;
+    umma_grouped_kernel<GROUP_BN, GROUP_STAGES><<<grid, 192, S::SMEM, s>>>(
+        probs, items, nitems, status);
+    return cudaGetLastError();
+}
+
+int group_tile_n() { return GROUP_BN; }
+
 }  // namespace cgh

@@ -123,4 +123,24 @@ __device__ __forceinline__ void tmem_ld_wait() {
 }
 
 }  // namespace umma
+
+// One problem of a grouped split GEMM: its four tensor maps (A hi, B hi,
+// A lo, B lo) live in global memory, 64-byte aligned, and are read by TMA.
+struct alignas(64) GroupProb {
+    CUtensorMap tA, tB, tA2, tB2;
+    float *D;
+    long long ldd;
+    int M, N, K;
+    float lo_scale;
+};
+
+// Fill gp (tensor maps and sizes) for the split GEMM `op`; false if a
+// tensor map cannot be encoded.
+bool encode_group_prob(GroupProb *gp, const GemmOperands &op);
+cudaError_t launch_umma_grouped(const GroupProb *probs, const uint2 *items,
+                                int nitems, unsigned *status, int sm_count,
+                                cudaStream_t s);
+cudaError_t prepare_umma_grouped();
+int group_tile_n();
+
 }  // namespace cgh

@@ -1,0 +1,157 @@
+"""cgh_batch: many holograms of uneven size, N and wavelength in one
+persistent, graph-replayed launch.  Each hologram must equal its own
+single-call result (bit for bit with the same tile shape, direct method) and
+match the FP64 oracle within the method's bound."""
+import numpy as np
+import pytest
+
+from gpu_util import max_abs, rel_rms, sample_rows, sum_abs_A, to_dev
+from workloads import batch_problems, make_cloud
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1002_0916_gb300 as cg
+    return cg
+
+
+@pytest.fixture
+def h(cg):
+    handle = cg.cgh_create(0)
+    yield handle
+    cg.cgh_destroy(handle)
+
+
+def _problems(clouds):
+    import torch
+    probs = []
+    for c in clouds:
+        pts, A, z = to_dev(c)
+        out = torch.full((c.Ny, c.Nx), float("nan"), device="cuda")
+        probs.append(dict(points=pts, A=A, z=z, lam=c.lam, p=c.p, Nx=c.Nx,
+                          Ny=c.Ny, out=out))
+    return probs
+
+
+def _small_clouds():
+    lams = (633e-9, 532e-9, 473e-9)
+    shapes = [(97, 61, 257), (128, 128, 64), (33, 200, 1), (300, 17, 129),
+              (64, 64, 0), (250, 190, 500), (5, 3, 31)]
+    return [make_cloud(500 + i, N, Nx, Ny, integer=(i % 2 == 0), zlo=0.3,
+                       zhi=1.2, lam=lams[i % 3], p=8e-6)
+            for i, (Nx, Ny, N) in enumerate(shapes)]
+
+
+def test_direct_batch_equals_single_calls(cg, h, oracle_mod):
+    import torch
+    clouds = _small_clouds()
+    probs = _problems(clouds)
+    tile = cg.cgh_direct_tiles()[0]
+    cg.cgh_set_direct_tile(h, tile)
+    cg.cgh_batch(probs, method="direct", handle=h)
+    torch.cuda.synchronize()
+    assert cg.cgh_last_device_status(h) == cg.CGH_OK
+    for c, pr in zip(clouds, probs):
+        got = pr["out"].cpu().numpy()
+        pts, A, z = to_dev(c)
+        single = cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, handle=h)
+        assert np.array_equal(got, single.cpu().numpy())
+        if c.N:
+            assert max_abs(got, oracle_mod.forward(c)) <= 1e-4 * sum_abs_A(c)
+        else:
+            assert np.all(got == 0)
+
+
+def test_graph_replay_rereads_inputs(cg, h, oracle_mod):
+    import torch
+    clouds = _small_clouds()[:4]
+    probs = _problems(clouds)
+    cg.cgh_batch(probs, handle=h)
+    n0 = cg.cgh_launch_count(h)
+    cg.cgh_batch(probs, handle=h)            # replay of the cached graph
+    assert cg.cgh_launch_count(h) - n0 == 3
+    first = [pr["out"].clone() for pr in probs]
+    # new amplitudes in the same buffers: the replay must see them
+    for pr in probs:
+        pr["A"].mul_(0.5)
+    cg.cgh_batch(probs, handle=h)
+    torch.cuda.synchronize()
+    for f, pr in zip(first, probs):
+        assert torch.allclose(pr["out"], 0.5 * f, rtol=1e-5, atol=1e-5)
+
+
+def test_batch_captured_by_caller(cg, h):
+    import torch
+    clouds = _small_clouds()[:3]
+    probs = _problems(clouds)
+    cg.cgh_batch(probs, handle=h)  # sizes the workspace outside the capture
+    torch.cuda.synchronize()
+    ref = [pr["out"].clone() for pr in probs]
+    for pr in probs:
+        pr["out"].fill_(float("nan"))
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            cg.cgh_batch(probs, handle=h, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    for r, pr in zip(ref, probs):
+        assert torch.equal(r, pr["out"])
+
+
+def test_batch_argument_errors(cg, h):
+    clouds = _small_clouds()[:2]
+    probs = _problems(clouds)
+    probs[1]["lam"] = -1.0
+    with pytest.raises(cg.CGHError) as e:
+        cg.cgh_batch(probs, handle=h)
+    assert e.value.status == cg.CGH_ERR_INVALID_ARG
+    assert "problem 1" in str(e.value)
+    import ctypes
+    assert cg.lib.cgh_batch(h, None, 0, 0, None) == cg.CGH_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("method", ["direct", "sep_fp16x3"])
+def test_batch64_uneven_workload(cg, h, oracle_mod, method):
+    """64 holograms, Nx, Ny in {512..2048 step 128}, N in [100, 8192], three
+    wavelengths: the batched workload at full size, one call; oracle on
+    sampled rows of sampled problems."""
+    import torch
+    clouds = batch_problems(seed=0)
+    probs = _problems(clouds)
+    try:
+        cg.cgh_batch(probs, method=method, handle=h)
+    except cg.CGHError as e:
+        if e.status == cg.CGH_ERR_UNSUPPORTED:
+            pytest.skip("method not built")
+        raise
+    torch.cuda.synchronize()
+    assert cg.cgh_last_device_status(h) == cg.CGH_OK
+    rng = np.random.default_rng(8)
+    for i in rng.choice(len(clouds), 6, replace=False):
+        c = clouds[i]
+        got = probs[i]["out"].cpu().numpy()
+        assert np.all(np.isfinite(got))
+        rows = sample_rows(c.Ny, 2, seed=int(i))
+        ref = oracle_mod.forward(c, rows=rows)
+        if method == "direct":
+            assert max_abs(got[rows], ref) <= 1e-4 * sum_abs_A(c)
+        else:
+            assert rel_rms(got[rows], ref) <= 1e-4
+
+
+def test_tune_batch(cg, h):
+    import torch
+    clouds = _small_clouds()
+    probs = _problems(clouds)
+    tile = cg.cgh_tune_batch(h, probs)
+    assert tile in cg.cgh_direct_tiles()
+    cg.cgh_batch(probs, handle=h)
+    torch.cuda.synchronize()
+    assert cg.cgh_last_device_status(h) == cg.CGH_OK
