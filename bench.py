@@ -50,6 +50,11 @@ def parse_args():
                     help="host time budget of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--methods", default="direct,sep_fp16x3")
+    ap.add_argument("--workload", default="paper",
+                    choices=["paper", "large", "batch64", "adjoint"],
+                    help="paper: 1920x1024x1024 (the headline line); large: "
+                         "3840x2160x16384; batch64: 64 uneven holograms; adjoint: "
+                         "1920x1080x4096 forward + adjoint")
     return ap.parse_args()
 
 
@@ -61,7 +66,7 @@ def workload_desc():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,"
@@ -76,12 +81,14 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples; those taken in [t0, t1] (host time) if any
+        landed there, else those of the loaded run just before."""
         if self.proc is None:
             return None
         time.sleep(0.25)
@@ -91,51 +98,70 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        import datetime
         rows = []
         for ln in out.splitlines():
             parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
         if not rows:
             return None
+        window = "timed region"
+        sel = [r for r in rows if t0 is not None and t0 - 0.05 <= r[0] <= t1 + 0.05]
+        if not sel:
+            window = "load just before the timed region (same work)"
+            sel = [r for r in rows if t0 is None or r[0] <= t0]
+            sel = sel[-5:] if sel else rows
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i in range(4)
+        reasons = sorted({names[i] for _, _, _, r in sel for i in range(4)
                           if r[i].lower().startswith("active")})
-        max_mhz = max(r[1] for r in rows)
-        loaded = [r[0] for r in rows if r[0] > 0.5 * max_mhz] or [r[0] for r in rows]
-        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max_mhz,
-                "reasons": reasons, "samples": len(rows)}
+        max_mhz = max(r[2] for r in rows)
+        return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": max_mhz,
+                "reasons": reasons, "samples": len(sel), "window": window}
 
 
 # ------------------------------------------------------------ cpu baseline
-def cpu_baseline(cloud, seconds: float, tag: str = "cpu_baseline"):
-    """Time the FP64 oracle on evenly spaced rows of the workload, sized to
-    about `seconds` of host work (all cores)."""
+def _oracle_rows_for(cloud, seconds):
+    """Evenly spaced rows (and whole-frame repeats) worth about `seconds` of
+    oracle time on all host cores."""
     import numpy as np
 
     import oracle
+    probe = np.linspace(0, cloud.Ny - 1, min(cloud.Ny, 32)).round().astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.forward(cloud, rows=probe)
+    per_row = (time.perf_counter() - t0) / len(probe)
+    nrows = int(max(1, min(cloud.Ny, seconds / max(per_row, 1e-6))))
+    rows = np.unique(np.linspace(0, cloud.Ny - 1, nrows).round().astype(np.int32))
+    reps = 1
+    if len(rows) == cloud.Ny:
+        reps = max(1, int(seconds / max(per_row * cloud.Ny, 1e-6)))
+    return rows, reps
+
+
+def cpu_baseline(cloud, seconds: float):
+    """Time the FP64 oracle, as it stands, on about `seconds` of the workload
+    (evenly spaced rows, or whole frames repeated), all host cores."""
+    import oracle
     oracle.build()
     cores = oracle.max_threads()
-    probe_rows = np.arange(0, cloud.Ny, max(1, cloud.Ny // 4))[:4].astype(np.int32)
+    rows, reps = _oracle_rows_for(cloud, seconds)
     t0 = time.perf_counter()
-    oracle.forward(cloud, rows=probe_rows)
-    per_row = (time.perf_counter() - t0) / len(probe_rows)
-    nrows = int(max(1, min(cloud.Ny, seconds / max(per_row, 1e-6))))
-    rows = np.linspace(0, cloud.Ny - 1, nrows).round().astype(np.int32)
-    rows = np.unique(rows)
-    t0 = time.perf_counter()
-    oracle.forward(cloud, rows=rows)
+    for _ in range(reps):
+        oracle.forward(cloud, rows=rows)
     dt = time.perf_counter() - t0
-    pp = len(rows) * cloud.Nx * cloud.N
+    pp = reps * len(rows) * cloud.Nx * cloud.N
+    what = (f"{len(rows)} of {cloud.Ny} rows (evenly spaced)" if reps == 1 else
+            f"the whole frame {reps} times")
     return {"value": pp / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(rows)} of {cloud.Ny} rows (evenly spaced) of the "
-                      f"{cloud.Nx}x{cloud.Ny}x{cloud.N} hologram, FP64 Eq. 1, "
-                      f"OpenMP over rows; {dt:.2f} s"}
+            "sample": f"{what} of the {cloud.Nx}x{cloud.Ny}x{cloud.N} hologram, "
+                      f"FP64 Eq. 1, OpenMP over rows; {dt:.2f} s"}
 
 
 # -------------------------------------------------------------- reference
@@ -151,13 +177,8 @@ def run_reference(args):
     c = workload(WORKLOAD)
     cores = oracle.max_threads()
     # one step: a bounded row sample sized so the run takes ~2 minutes
-    probe = np.arange(0, c.Ny, c.Ny // 4)[:4].astype(np.int32)
-    t0 = time.perf_counter()
-    oracle.forward(c, rows=probe)
-    per_row = (time.perf_counter() - t0) / len(probe)
     budget = 120.0 / max(1, args.steps + args.warmup)
-    nrows = int(max(1, min(c.Ny, budget / max(per_row, 1e-6))))
-    rows = np.linspace(0, c.Ny - 1, nrows).round().astype(np.int32)
+    rows, _ = _oracle_rows_for(c, budget)
     for _ in range(args.warmup):
         oracle.forward(c, rows=rows)
     times = []
@@ -208,6 +229,76 @@ def _traffic_for(kernel: str):
     return rec.get("dram_bytes_per_launch")
 
 
+class Leg:
+    """One piece of a step: a callable that enqueues its work on the stream,
+    the point-pixel updates it performs, and the tensor-core flops (if any)
+    of its GEMM launches."""
+
+    def __init__(self, name, fn, pp, gemm_flops=0.0, gemm_launches=0):
+        self.name, self.fn, self.pp = name, fn, pp
+        self.gemm_flops, self.gemm_launches = gemm_flops, gemm_launches
+
+
+def build_legs(cg, h, which, methods, dev, stream):
+    """The legs of one step of workload `which` (tensors on `dev`)."""
+    import torch
+
+    from workloads import batch_problems, grad_field, workload
+
+    def dev_cloud(c):
+        return (torch.from_numpy(c.xy).to(dev), torch.from_numpy(c.A).to(dev),
+                torch.from_numpy(c.z).to(dev))
+
+    legs = []
+    if which in ("paper", "large"):
+        c = workload(WORKLOAD if which == "paper" else "cfg3_3840x2160_n16384")
+        pts, A, z = dev_cloud(c)
+        for m in methods:
+            out = torch.empty((c.Ny, c.Nx), dtype=torch.float32, device=dev)
+            fn = (lambda m=m, out=out: cg.cgh_forward(
+                pts, A, z, c.lam, c.p, c.Nx, c.Ny, out=out, method=m, handle=h,
+                stream=stream))
+            mult = {"sep_fp16x3": 3.0, "sep_fp16": 1.0, "sep_bf16": 1.0}.get(m, 0.0)
+            legs.append(Leg(m, fn, c.pp, 4.0 * c.pp * mult, 1 if mult else 0))
+        return c, legs
+    if which == "batch64":
+        clouds = batch_problems(seed=0)
+        probs = []
+        for cl in clouds:
+            p_, A_, z_ = dev_cloud(cl)
+            probs.append(dict(points=p_, A=A_, z=z_, lam=cl.lam, p=cl.p, Nx=cl.Nx,
+                              Ny=cl.Ny, out=torch.empty((cl.Ny, cl.Nx),
+                                                        dtype=torch.float32,
+                                                        device=dev)))
+        pp = sum(cl.pp for cl in clouds)
+        for m in methods:
+            if m not in ("direct", "sep_fp16x3"):
+                continue
+            fn = (lambda m=m: cg.cgh_batch(probs, method=m, handle=h, stream=stream))
+            legs.append(Leg("batch_" + m, fn, pp))
+        return clouds[0], legs
+    if which == "adjoint":
+        c = workload("cfg5_1920x1080_n4096")
+        pts, A, z = dev_cloud(c)
+        G = torch.from_numpy(grad_field(11, c.Nx, c.Ny, scale=40.0)).to(dev)
+        for m in methods:
+            if m not in ("direct", "sep_fp16x3"):
+                continue
+            out = torch.empty((c.Ny, c.Nx), dtype=torch.float32, device=dev)
+            f_fwd = (lambda m=m, out=out: cg.cgh_forward(
+                pts, A, z, c.lam, c.p, c.Nx, c.Ny, out=out, method=m, handle=h,
+                stream=stream))
+            f_bwd = (lambda m=m: cg.cgh_backward(
+                pts, A, z, c.lam, c.p, c.Nx, c.Ny, G, method=m, handle=h,
+                stream=stream))
+            mult = 3.0 if m == "sep_fp16x3" else 0.0
+            legs.append(Leg(m + "_fwd", f_fwd, c.pp, 4.0 * c.pp * mult, 1 if mult else 0))
+            legs.append(Leg(m + "_bwd", f_bwd, c.pp, 2 * 4.0 * c.pp * mult,
+                            2 if mult else 0))
+        return c, legs
+    raise SystemExit(f"unknown workload {which}")
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -228,30 +319,22 @@ def run_ours(args):
             dist.barrier()
 
     import paper_1002_0916_gb300 as cg
-    from workloads import workload
 
-    c = workload(WORKLOAD)
     dev = torch.device("cuda", local)
-    pts = torch.from_numpy(c.xy).to(dev)
-    A = torch.from_numpy(c.A).to(dev)
-    z = torch.from_numpy(c.z).to(dev)
     h = cg.cgh_create(local)
     stream = torch.cuda.current_stream()
-
-    methods = []
-    outs = {}
-    for m in [s.strip() for s in args.methods.split(",") if s.strip()]:
-        out = torch.empty((c.Ny, c.Nx), dtype=torch.float32, device=dev)
+    methods = [m.strip() for m in args.methods.split(",") if m.strip()]
+    c, all_legs = build_legs(cg, h, args.workload, methods, dev, stream)
+    legs = []
+    for leg in all_legs:            # first call: sizes workspaces, builds graphs
         try:
-            cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, out=out, method=m,
-                           handle=h)
+            leg.fn()
         except cg.CGHError as e:
             if e.status == cg.CGH_ERR_UNSUPPORTED:
                 continue
             raise
-        methods.append(m)
-        outs[m] = out
-    if not methods:
+        legs.append(leg)
+    if not legs:
         raise SystemExit("no GPU method available")
     torch.cuda.synchronize()
     if cg.cgh_last_device_status(h) != cg.CGH_OK:
@@ -261,9 +344,8 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB
 
     def step(evs=None):
-        for i, m in enumerate(methods):
-            cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, out=outs[m],
-                           method=m, handle=h, stream=stream)
+        for i, leg in enumerate(legs):
+            leg.fn()
             if evs is not None:
                 evs[i + 1].record(stream)
 
@@ -276,26 +358,34 @@ def run_ours(args):
     sampler = ClockSampler(f"GPU-{props.uuid}" if getattr(props, "uuid", None)
                            else str(local))
     K = args.steps
-    evsets = [[torch.cuda.Event(enable_timing=True) for _ in range(len(methods) + 1)]
+    evsets = [[torch.cuda.Event(enable_timing=True) for _ in range(len(legs) + 1)]
               for _ in range(K)]
     barrier()
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
+    # keep the GPU busy with the same work while the sampler warms up, so
+    # that the clock samples nearest the timed region are under this load
+    t_end = time.perf_counter() + 0.5
+    while time.perf_counter() < t_end:
+        step()
+        torch.cuda.synchronize()
     cg.cgh_kernel_timing(h, True)
     n0 = cg.cgh_launch_count(h)
+    t0 = time.time()
     for k in range(K):
         flush.zero_()                       # L2 flush between timed steps
         evsets[k][0].record(stream)
         step(evsets[k])
     torch.cuda.synchronize()
+    t1 = time.time()
     launches = cg.cgh_launch_count(h) - n0
     barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop(t0, t1)
 
     step_ms = [evs[0].elapsed_time(evs[-1]) for evs in evsets]
-    meth_ms = {m: [evs[i].elapsed_time(evs[i + 1]) for evs in evsets]
-               for i, m in enumerate(methods)}
+    leg_ms = {leg.name: statistics.mean(evs[i].elapsed_time(evs[i + 1]) for evs in evsets)
+              for i, leg in enumerate(legs)}
     kt = {name: cg.cgh_kernel_time(h, name) for name in cg.KERNELS}
     cg.cgh_kernel_timing(h, False)
     ms = statistics.mean(step_ms)
@@ -306,8 +396,8 @@ def run_ours(args):
         lt = torch.tensor([float(launches)], device=dev)
         dist.all_reduce(lt, op=dist.ReduceOp.SUM)
         launches = int(lt.item())
-    pp = c.pp
-    value = world * len(methods) * pp / (ms / 1e3)
+    pp_step = sum(leg.pp for leg in legs)
+    value = world * pp_step / (ms / 1e3)
 
     # ---- roofline of the dominant kernel
     dom = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
@@ -317,23 +407,28 @@ def run_ours(args):
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
     sms = props.multi_processor_count
-    if dom in ("direct", "naive"):
-        achieved = pp / (dom_ms / 1e3) / 1e9
-        peak = sms * MUFU_PER_CLK_PER_SM * NOMINAL_MAX_MHZ * 1e6 / 1e9
+    if dom in ("direct", "naive", "batch", "bwd_direct"):
+        # one cosine per update (two MUFU ops, sin and cos, for the adjoint)
+        mufu_per_pp = 2 if dom == "bwd_direct" else 1
+        pp_dom = {"direct": c.pp, "naive": c.pp, "bwd_direct": c.pp,
+                  "batch": max((leg.pp for leg in legs if leg.name.startswith("batch_direct")),
+                               default=c.pp)}[dom]
+        achieved = pp_dom / (dom_ms / 1e3) / 1e9
+        peak = sms * MUFU_PER_CLK_PER_SM * NOMINAL_MAX_MHZ * 1e6 / 1e9 / mufu_per_pp
         roof = {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Gpp/s", "frac": achieved / peak,
                 "peak_source": (f"derived: {sms} SMs x {MUFU_PER_CLK_PER_SM} MUFU "
-                                f"cosines/clk/SM x {NOMINAL_MAX_MHZ:.0f} MHz max SM "
-                                "clock (one cosine per point-pixel update)")}
+                                f"ops/clk/SM x {NOMINAL_MAX_MHZ:.0f} MHz max SM clock"
+                                f" / {mufu_per_pp} MUFU op(s) per point-pixel update")}
         if clocks and clocks.get("sm_mhz"):
             roof["frac_at_observed_clock"] = achieved / (
-                sms * MUFU_PER_CLK_PER_SM * clocks["sm_mhz"] * 1e6 / 1e9)
-    elif dom == "gemm":
-        mult = 3 if "sep_fp16x3" in methods else 1
-        flops = 4.0 * c.N * c.Nx * c.Ny * mult
-        achieved = flops / (dom_ms / 1e3) / 1e12
+                sms * MUFU_PER_CLK_PER_SM * clocks["sm_mhz"] * 1e6 / 1e9 / mufu_per_pp)
+    elif dom in ("gemm", "bwd_gemm"):
+        flops = sum(leg.gemm_flops for leg in legs)
+        nl = sum(leg.gemm_launches for leg in legs)
+        achieved = (flops / max(nl, 1)) / (dom_ms / 1e3) / 1e12
         base = peaks.get("bf16_tflops")
-        src = "of measured (MEASURED_PEAKS.json bf16 burst; FP16 rate equal)"
+        src = "of measured (MEASURED_PEAKS.json bf16 burst; FP16 dense rate equal)"
         if base is None:
             base, src = 1900.0, "of fallback (1.9 PFLOP/s bf16)"
         peak = base * FP16_OVER_BF16
@@ -344,61 +439,63 @@ def run_ours(args):
                 "unit": "GB/s", "frac": None}
     roof["kernel"] = dom
     roof["ms_per_launch"] = dom_ms
-    kernel_src = {"direct": "paper_1002_0916_gb300/csrc/direct.cu",
-                  "gemm": "paper_1002_0916_gb300/csrc/umma.cu"}.get(dom)
-    roof["traffic"] = _traffic_for(dom) if kernel_src else None
+    roof["traffic"] = _traffic_for(dom)
 
-    # ---- end to end through the host-buffer C-ABI call
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
-    hp, hA, hz = pin(c.xy), pin(c.A), pin(c.z)
-    hout = {m: torch.empty((c.Ny, c.Nx), dtype=torch.float32).pin_memory()
-            for m in methods}
-    for m in methods:
-        cg.cgh_forward_host(hp, hA, hz, c.lam, c.p, c.Nx, c.Ny, out=hout[m],
-                            method=m, handle=h, stream=stream)
-    barrier()
-    E = max(3, K // 2)
-    t0 = time.perf_counter()
-    for _ in range(E):
-        for m in methods:
+    # ---- end to end through the host-buffer C-ABI call (forward legs)
+    e2e = None
+    fwd_methods = [leg.name for leg in legs if leg.name in cg.METHODS]
+    if fwd_methods and args.workload in ("paper", "large"):
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        hp, hA, hz = pin(c.xy), pin(c.A), pin(c.z)
+        hout = {m: torch.empty((c.Ny, c.Nx), dtype=torch.float32).pin_memory()
+                for m in fwd_methods}
+        for m in fwd_methods:
             cg.cgh_forward_host(hp, hA, hz, c.lam, c.p, c.Nx, c.Ny, out=hout[m],
                                 method=m, handle=h, stream=stream)
-    e2e_s = (time.perf_counter() - t0) / E
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * len(methods) * pp / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": len(methods) * c.N * 16,
-           "d2h_bytes_per_step": len(methods) * c.Nx * c.Ny * 4,
-           "ms_per_step": e2e_s * 1e3}
+        barrier()
+        E = max(3, K // 2)
+        t0 = time.perf_counter()
+        for _ in range(E):
+            for m in fwd_methods:
+                cg.cgh_forward_host(hp, hA, hz, c.lam, c.p, c.Nx, c.Ny, out=hout[m],
+                                    method=m, handle=h, stream=stream)
+        e2e_s = (time.perf_counter() - t0) / E
+        if dist is not None:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * len(fwd_methods) * c.pp / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": len(fwd_methods) * c.N * 16,
+               "d2h_bytes_per_step": len(fwd_methods) * c.Nx * c.Ny * 4,
+               "ms_per_step": e2e_s * 1e3}
 
     line = None
     if rank == 0:
+        cfg = {"workload": workload_desc() if args.workload == "paper" else args.workload,
+               "methods": [leg.name for leg in legs],
+               "l2": "flushed: 256 MiB device write between timed steps",
+               "parallelism": ("replicas (each rank its own copy of the workload)"
+                               if world > 1 else "single GPU")}
+        if args.workload != "batch64":
+            cfg.update({"Nx": c.Nx, "Ny": c.Ny, "N": c.N})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if methods == ["direct"] else "f32+f16x3",
-            "data": "synthetic",
-            "config": {"workload": workload_desc(), "Nx": c.Nx, "Ny": c.Ny,
-                       "N": c.N, "methods": methods,
-                       "l2": "flushed: 256 MiB device write between timed steps",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "methods": {m: {"ms_per_cgh": statistics.mean(meth_ms[m]),
-                            "pp_per_s": pp / (statistics.mean(meth_ms[m]) / 1e3)}
-                        for m in methods},
-            "kernels_ms_per_launch": {k: kt[k][0] / kt[k][1]
-                                      for k in kt if kt[k][1] > 0},
-            "roofline": roof, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks,
+            "dtype": "f32+f16x3" if any("sep" in leg.name for leg in legs) else "f32",
+            "data": "synthetic", "config": cfg,
+            "methods": {leg.name: {"ms": leg_ms[leg.name],
+                                   "pp_per_s": leg.pp / (leg_ms[leg.name] / 1e3)}
+                        for leg in legs},
+            "kernels_ms_per_launch": {k: kt[k][0] / kt[k][1] for k in kt if kt[k][1] > 0},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
     cg.cgh_destroy(h)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and args.workload == "paper":
             line["cpu_baseline"] = cpu_baseline(c, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     return 0

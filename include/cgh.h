@@ -196,6 +196,9 @@ typedef struct {
     int vec_x;             /* pixels per thread along x        */
     int vec_y;             /* pixels per thread along y        */
     int points_per_stage;  /* points per shared-memory stage   */
+    int poly_pixels;       /* pixels per thread whose cosine is a
+                              polynomial on the FMA pipe instead of
+                              the MUFU (special-function) unit     */
 } cgh_direct_tile;
 
 /* Number of direct-kernel tile shapes compiled into this build, and the
@@ -271,6 +274,19 @@ const char *cgh_last_error(cgh_handle h);
 cgh_status cgh_debug_gemm(cgh_handle h, const void *A, const void *B,
                           float *D, int M, int N, int K, int is_bf16,
                           void *stream);
+
+/* Diagnostic for failure handling: launch one CTA that waits on an mbarrier
+ * nothing ever arrives at.  The wait gives up after limit_cycles SM clock
+ * cycles (clamped to [1e6, 4e9]), records CGH_ERR_TIMEOUT in the device
+ * status word (read it with cgh_last_device_status) and the kernel exits;
+ * the context stays usable.  This is the same bounded-wait path as every
+ * pipelined kernel of the library.
+ *
+ * Host-side fault injection: if the environment variable
+ * CGH_FAIL_ALLOC_AFTER=n is set when a handle is created, that handle's
+ * (n+1)-th workspace allocation fails with CGH_ERR_NOMEM. */
+cgh_status cgh_debug_stalled_wait(cgh_handle h, long long limit_cycles,
+                                  void *stream);
 
 #ifdef __cplusplus
 }

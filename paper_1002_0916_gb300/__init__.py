@@ -51,7 +51,7 @@ class CGHError(RuntimeError):
 class _Tile(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("vec_x", ctypes.c_int), ("vec_y", ctypes.c_int),
-                ("points_per_stage", ctypes.c_int)]
+                ("points_per_stage", ctypes.c_int), ("poly_pixels", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -92,6 +92,8 @@ def _load():
     L.cgh_last_error.argtypes = [vp]
     L.cgh_last_error.restype = ctypes.c_char_p
     L.cgh_debug_gemm.argtypes = [vp, fp, fp, fp, ci, ci, ci, ci, vp]
+    L.cgh_debug_stalled_wait.argtypes = [vp, ctypes.c_longlong, vp]
+    L.cgh_debug_stalled_wait.restype = ci
     L.cgh_forward_noalloc.argtypes = [fp, fp, fp, ci, cd, cd, ci, ci, fp, vp]
     L.cgh_forward_noalloc.restype = ci
     L.cgh_kernel_timing.argtypes = [vp, ci]
@@ -303,7 +305,7 @@ def cgh_tune_batch(h, problems: Sequence[dict], method="direct", stream=None):
     st = _L().cgh_tune_batch(h, arr, n, _method(method), _stream_ptr(stream),
                              ctypes.byref(t))
     _check(h, st, "cgh_tune_batch")
-    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage)
+    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels)
 
 
 # ---------------------------------------------------------- tiles/tuning
@@ -312,7 +314,8 @@ def cgh_direct_tiles():
     for i in range(_L().cgh_direct_tile_count()):
         t = _Tile()
         _L().cgh_direct_tile_get(i, ctypes.byref(t))
-        out.append((t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage))
+        out.append((t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage,
+                    t.poly_pixels))
     return out
 
 
@@ -330,7 +333,7 @@ def cgh_tune(h, N: int, Nx: int, Ny: int, method="direct", stream=None):
     st = _L().cgh_tune(h, int(N), int(Nx), int(Ny), _method(method),
                       _stream_ptr(stream), ctypes.byref(t))
     _check(h, st, "cgh_tune")
-    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage)
+    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels)
 
 
 def cgh_last_device_status(h, stream=None) -> int:

@@ -4,6 +4,7 @@
 // map onto cgh_create / cgh_forward(_host) / cgh_destroy.
 #include <math.h>
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -67,6 +68,10 @@ cgh_status cgh_ctx::ensure(Buffer &b, size_t bytes, cudaStream_t s,
     }
     size_t want = bytes + bytes / 8;  // some headroom for nearby shapes
     want = (want + 4095) & ~(size_t)4095;
+    if (fail_alloc_after == 0)
+        return fail(CGH_ERR_NOMEM, "%s: injected allocation failure (CGH_FAIL_ALLOC_AFTER)",
+                    what);
+    if (fail_alloc_after > 0) --fail_alloc_after;
     cudaError_t e = cudaMalloc(&b.ptr, want);
     if (e != cudaSuccess) {
         b.ptr = nullptr;
@@ -312,6 +317,7 @@ cgh_status cgh_create(cgh_handle *out, int device) {
         return CGH_ERR_CUDA;
     }
     h->load_tune_cache();
+    if (const char *f = getenv("CGH_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(f);
     *out = h;
     return CGH_OK;
 }
@@ -445,6 +451,7 @@ cgh_status cgh_direct_tile_get(int i, cgh_direct_tile *out) {
     out->vec_x = t.vx;
     out->vec_y = t.vy;
     out->points_per_stage = t.pt;
+    out->poly_pixels = t.np;
     return CGH_OK;
 }
 
@@ -455,13 +462,48 @@ cgh_status cgh_set_direct_tile(cgh_handle h, const cgh_direct_tile *tile) {
         return CGH_OK;
     }
     DirectTile t{tile->tile_x, tile->tile_y, tile->vec_x, tile->vec_y,
-                 tile->points_per_stage};
+                 tile->points_per_stage, tile->poly_pixels};
     int i = direct_tile_index(t);
     if (i < 0)
-        return h->fail(CGH_ERR_UNSUPPORTED, "tile %dx%d/%dx%d/%d not compiled in",
-                       t.tx, t.ty, t.vx, t.vy, t.pt);
+        return h->fail(CGH_ERR_UNSUPPORTED, "tile %dx%d/%dx%d/%d/%d not compiled in",
+                       t.tx, t.ty, t.vx, t.vy, t.pt, t.np);
     h->forced_tile = i;
     return CGH_OK;
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ fault injection
+// A CTA that waits on an mbarrier nothing ever arrives at.  The wait gives
+// up after `limit` cycles, records DEV_TIMEOUT and the kernel returns: the
+// bounded-wait path every pipelined kernel of this library uses.
+__global__ void stalled_wait_kernel(long long limit, unsigned *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t0 = clock64();
+        bool done = false;
+        while (!(done = mbar_try_wait(&bar, 0))) {
+            if (clock64() - t0 > limit) break;
+        }
+        if (!done) set_status(status, DEV_TIMEOUT);
+    }
+}
+
+extern "C" cgh_status cgh_debug_stalled_wait(cgh_handle h, long long limit_cycles,
+                                             void *stream) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (limit_cycles < 1000000LL) limit_cycles = 1000000LL;
+    if (limit_cycles > 4000000000LL) limit_cycles = 4000000000LL;
+    TimedLaunch tl(h, CGH_K_AUX, (cudaStream_t)stream);
+    stalled_wait_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(limit_cycles, h->d_status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return h->cuda_fail(e, "stalled-wait launch");
+    tl.done();
+    return CGH_OK;
+}

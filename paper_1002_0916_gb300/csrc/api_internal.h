@@ -61,6 +61,9 @@ struct cgh_ctx {
     void timer_reset();
 
     int forced_tile = -1;                         // direct tile override
+    // fault injection: workspace allocations left before one is made to
+    // fail (-1: never); set from CGH_FAIL_ALLOC_AFTER at cgh_create
+    int fail_alloc_after = -1;
     std::unordered_map<std::string, int> tuned;   // size bucket -> tile
 
     cgh_status fail(cgh_status st, const char *fmt, ...);

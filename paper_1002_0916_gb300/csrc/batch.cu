@@ -62,12 +62,12 @@ __global__ void batch_tables_kernel(const BatchPrep *__restrict__ prep) {
                            b.phy, b.amp);
 }
 
-template <int TX, int TY, int VX, int VY, int PT, int NST>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP>
 __global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST>::THREADS)
 direct_batch_kernel(const BatchTile *__restrict__ probs,
                     const uint2 *__restrict__ items, int nitems,
                     unsigned *counter, unsigned *status) {
-    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST>;
+    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;
@@ -102,14 +102,14 @@ direct_batch_kernel(const BatchTile *__restrict__ probs,
     }
 }
 
-template <int TX, int TY, int VX, int VY, int PT, int NST>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP>
 static cudaError_t launch_batch_t(const BatchTile *probs, const uint2 *items,
                                   int nitems, unsigned *counter, unsigned *status,
                                   int sm_count, cudaStream_t s) {
     // probs == nullptr: only set the kernel's attributes and cache its
     // occupancy (done before any capture)
     using S = DirectShape<TX, TY, VX, VY, PT, NST>;
-    auto kern = direct_batch_kernel<TX, TY, VX, VY, PT, NST>;
+    auto kern = direct_batch_kernel<TX, TY, VX, VY, PT, NST, NP>;
     // attribute and occupancy once per device (no such calls inside a capture
     // of a geometry that has run before)
     static int per_sm_cache[64] = {};
@@ -137,10 +137,11 @@ static cudaError_t launch_batch(int tile_index, const BatchTile *probs,
                                 const uint2 *items, int nitems, unsigned *counter,
                                 unsigned *status, int sm_count, cudaStream_t s) {
     int i = 0;
-#define X(tx, ty, vx, vy, pt, ns)                                                  \
-    if (tile_index == i)                                                           \
-        return launch_batch_t<tx, ty, vx, vy, pt, ns>(probs, items, nitems, counter, \
-                                                      status, sm_count, s);         \
+#define X(tx, ty, vx, vy, pt, ns, np)                                           \
+    if (tile_index == i)                                                        \
+        return launch_batch_t<tx, ty, vx, vy, pt, ns, np>(probs, items, nitems,  \
+                                                          counter, status,      \
+                                                          sm_count, s);         \
     ++i;
     CGH_DIRECT_TILES(X)
 #undef X
@@ -478,6 +479,7 @@ extern "C" cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs,
             chosen->vec_x = t.vx;
             chosen->vec_y = t.vy;
             chosen->points_per_stage = t.pt;
+            chosen->poly_pixels = t.np;
         }
     }
     if (prev != h->device) cudaSetDevice(prev);

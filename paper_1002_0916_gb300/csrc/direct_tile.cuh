@@ -4,19 +4,24 @@
 #pragma once
 
 #include "common.cuh"
+#include "cos_poly.h"
 
 namespace cgh {
 
-// The tile shapes compiled in: X(TX, TY, VX, VY, PT, NST) = pixels per CTA
-// along x and y, pixels per thread along x and y, points per shared-memory
-// stage, stages.  Every shape has 256 threads per CTA.
+// The tile shapes compiled in: X(TX, TY, VX, VY, PT, NST, NP) = pixels per
+// CTA along x and y, pixels per thread along x and y, points per
+// shared-memory stage, stages, and how many of each thread's VX * VY pixels
+// take the FMA-pipe cosine polynomial instead of the MUFU cosine (about a
+// quarter balances the two pipes).  Every shape has 256 threads per CTA.
 #define CGH_DIRECT_TILES(X)          \
-    X(64, 64, 4, 4, 32, 3)           \
-    X(64, 32, 4, 2, 32, 3)           \
-    X(128, 32, 4, 4, 32, 3)          \
-    X(32, 32, 2, 2, 64, 3)           \
-    X(128, 64, 8, 4, 16, 3)          \
-    X(64, 16, 4, 1, 64, 3)
+    X(64, 64, 4, 4, 32, 3, 4)        \
+    X(64, 64, 4, 4, 32, 3, 0)        \
+    X(64, 32, 4, 2, 32, 3, 2)        \
+    X(128, 32, 4, 4, 32, 3, 4)       \
+    X(32, 32, 2, 2, 64, 3, 1)        \
+    X(32, 32, 2, 2, 64, 3, 0)        \
+    X(128, 64, 8, 4, 16, 3, 8)       \
+    X(64, 16, 4, 1, 64, 3, 1)
 
 // ------------------------------------------------------------- tables
 // Entries of the per-axis angle tables of one problem: x angles laid out
@@ -91,6 +96,24 @@ struct VecLoad<8> {
     }
 };
 
+// cos(theta) for |theta| < 2 pi on the FMA pipe: fold to
+// d = min(|theta|, 2 pi - |theta|) in [0, pi] (cos is even and 2 pi
+// periodic), then the degree-6 polynomial in d^2 of cos_poly.h (max error
+// about 6e-7, like the hardware cosine's 2^-21.4 on [-pi, pi]).
+__device__ __forceinline__ float cos_poly(float th) {
+    const float a = fabsf(th);
+    const float d = fminf(a, 6.28318530717958647692f - a);
+    const float s = d * d;
+    float p = COS_C6;
+    p = fmaf(p, s, COS_C5);
+    p = fmaf(p, s, COS_C4);
+    p = fmaf(p, s, COS_C3);
+    p = fmaf(p, s, COS_C2);
+    p = fmaf(p, s, COS_C1);
+    p = fmaf(p, s, COS_C0);
+    return p;
+}
+
 template <int TX, int TY, int VX, int VY, int PT, int NST>
 struct DirectShape {
     static constexpr int NTX = TX / VX;
@@ -110,8 +133,9 @@ struct DirectShape {
 // (g0 + t)-th stage load of the CTA, so a persistent CTA can run many pixel
 // tiles back to back on the same NST-slot ring and mbarriers: slot
 // (g0 + t) % NST, barrier parity ((g0 + t) / NST) & 1.
-template <int TX, int TY, int VX, int VY, int PT, int NST>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP>
 struct DirectTileLoop {
+    static_assert(NP >= 0 && NP <= VX * VY, "polynomial pixels per thread");
     using S = DirectShape<TX, TY, VX, VY, PT, NST>;
 
     __device__ static void issue(float *smem, uint64_t *full, const float *gx,
@@ -163,8 +187,13 @@ struct DirectTileLoop {
 #pragma unroll
                     for (int i = 0; i < VY; ++i)
 #pragma unroll
-                        for (int k = 0; k < VX; ++k)
-                            acc[i][k] = fmaf(a, __cosf(vx[k] + vy[i]), acc[i][k]);
+                        for (int k = 0; k < VX; ++k) {
+                            const float th = vx[k] + vy[i];
+                            // the first NP pixels of the thread on the FMA
+                            // pipe, the rest on the MUFU (compile-time split)
+                            const float cs = (i * VX + k < NP) ? cos_poly(th) : __cosf(th);
+                            acc[i][k] = fmaf(a, cs, acc[i][k]);
+                        }
                 }
             }
             __syncthreads();  // every thread is done with slot s

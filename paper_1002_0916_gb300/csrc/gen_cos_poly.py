@@ -1,0 +1,67 @@
+#!/usr/bin/env python3
+"""Fit the software cosine used next to the hardware (MUFU) cosine in the
+direct kernels, and write cos_poly.h.
+
+cos(d) for d in [0, pi] as a polynomial in s = d^2 of degree 6, fitted by an
+iteratively reweighted least-squares minimax approximation (Lawson's
+algorithm: repeated weighted least squares whose weights grow where the error
+is largest) on a dense grid.  The kernels fold any angle |theta| < 2 pi into
+[0, pi] first (cos is even and 2 pi periodic).
+
+    python gen_cos_poly.py            # rewrite cos_poly.h beside this file
+    python gen_cos_poly.py --check    # print the error of the committed table
+"""
+import os
+import sys
+
+import numpy as np
+
+DEG = 6
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "cos_poly.h")
+
+
+def fit(deg=DEG, iters=200):
+    s = np.linspace(0.0, np.pi ** 2, 40001)
+    f = np.cos(np.sqrt(s))
+    V = np.vander(s, deg + 1, increasing=True)
+    w = np.ones_like(s)
+    for _ in range(iters):
+        c, *_ = np.linalg.lstsq(V * w[:, None], f * w, rcond=None)
+        e = np.abs(V @ c - f)
+        w = w * (e / e.max() + 1e-3)
+        w /= w.sum()
+    return c
+
+
+def fp32_error(c):
+    d = np.linspace(0.0, np.pi, 200001).astype(np.float32)
+    s = (d * d).astype(np.float32)
+    c32 = np.asarray(c, dtype=np.float32)
+    p = np.full_like(s, c32[-1])
+    for k in range(len(c32) - 2, -1, -1):
+        p = (p * s + c32[k]).astype(np.float32)
+    return float(np.max(np.abs(p.astype(np.float64) - np.cos(d.astype(np.float64)))))
+
+
+def main():
+    if "--check" in sys.argv:
+        txt = open(OUT).read()
+        vals = [float(t.split("=")[1].strip().rstrip("f;")) for t in txt.splitlines()
+                if "constexpr float COS_C" in t]
+        print(f"max |P(d^2) - cos d| on [0, pi] in FP32: {fp32_error(vals):.3e}")
+        return
+    c = fit()
+    lines = ["// cos_poly.h -- written by gen_cos_poly.py; do not edit.",
+             "// cos(d) ~= sum_k COS_Ck (d^2)^k for d in [0, pi] (Lawson minimax fit,",
+             f"// degree {DEG} in d^2; max error in FP32 evaluation {fp32_error(c):.2e}).",
+             "#pragma once", "", "namespace cgh {", ""]
+    for k, v in enumerate(c):
+        lines.append(f"constexpr float COS_C{k} = {float(np.float32(v))!r}f;")
+    lines += ["", "}  // namespace cgh", ""]
+    open(OUT, "w").write("\n".join(lines))
+    print(open(OUT).read())
+
+
+if __name__ == "__main__":
+    main()

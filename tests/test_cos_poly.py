@@ -1,0 +1,42 @@
+"""The FMA-pipe cosine polynomial of the direct kernels (cos_poly.h, fitted
+by gen_cos_poly.py): its error over the folded range [0, pi], evaluated in
+FP32 exactly as the kernel does, against FP64 cos."""
+import os
+import re
+
+import numpy as np
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "paper_1002_0916_gb300", "csrc", "cos_poly.h")
+
+
+def _coeffs():
+    txt = open(HDR).read()
+    return [np.float32(float(v)) for v in
+            re.findall(r"constexpr float COS_C\d+ = ([-0-9.e+]+)f;", txt)]
+
+
+def _kernel_cos(theta):
+    """The kernel's fold and Horner evaluation, in float32."""
+    c = _coeffs()
+    a = np.abs(theta.astype(np.float32))
+    d = np.minimum(a, np.float32(6.28318530717958647692) - a)
+    s = (d * d).astype(np.float32)
+    p = np.full_like(s, c[-1])
+    for k in range(len(c) - 2, -1, -1):
+        p = (p * s + c[k]).astype(np.float32)
+    return p
+
+
+def test_polynomial_error_bound():
+    # the kernel feeds it theta_x + theta_y, both in [-pi, pi)
+    th = np.linspace(-2 * np.pi + 1e-6, 2 * np.pi - 1e-6, 400001).astype(np.float32)
+    err = np.abs(_kernel_cos(th).astype(np.float64) - np.cos(th.astype(np.float64)))
+    assert err.max() < 1e-6
+
+
+def test_polynomial_has_the_taylor_leading_terms():
+    c = _coeffs()
+    assert len(c) == 7
+    assert abs(c[0] - 1.0) < 1e-6 and abs(c[1] + 0.5) < 1e-5
+    assert abs(c[2] - 1.0 / 24) < 1e-5
