@@ -199,6 +199,8 @@ typedef struct {
     int poly_pixels;       /* pixels per thread whose cosine is a
                               polynomial on the FMA pipe instead of
                               the MUFU (special-function) unit     */
+    int point_groups;      /* thread groups splitting each stage's
+                              points (partial sums added in order) */
 } cgh_direct_tile;
 
 /* Number of direct-kernel tile shapes compiled into this build, and the
@@ -230,8 +232,9 @@ typedef enum {
     CGH_K_BWD_DIRECT = 6,     /* direct adjoint point-owned sums        */
     CGH_K_BWD_GEMM = 7,       /* separable adjoint GEMMs + fused sums   */
     CGH_K_BWD_REDUCE = 8,     /* adjoint partial-sum reduction          */
-    CGH_K_BATCH = 9,          /* persistent batch kernel                */
+    CGH_K_BATCH = 9,          /* direct batch (its whole graph)         */
     CGH_K_AUX = 10,           /* small helpers (conversions, fills)     */
+    CGH_K_BATCH_SEP = 11,     /* separable batch (its whole graph)      */
     CGH_K_COUNT = 16
 } cgh_kernel_id;
 

@@ -51,7 +51,8 @@ class CGHError(RuntimeError):
 class _Tile(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("vec_x", ctypes.c_int), ("vec_y", ctypes.c_int),
-                ("points_per_stage", ctypes.c_int), ("poly_pixels", ctypes.c_int)]
+                ("points_per_stage", ctypes.c_int), ("poly_pixels", ctypes.c_int),
+                ("point_groups", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -305,7 +306,8 @@ def cgh_tune_batch(h, problems: Sequence[dict], method="direct", stream=None):
     st = _L().cgh_tune_batch(h, arr, n, _method(method), _stream_ptr(stream),
                              ctypes.byref(t))
     _check(h, st, "cgh_tune_batch")
-    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels)
+    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels,
+            t.point_groups)
 
 
 # ---------------------------------------------------------- tiles/tuning
@@ -315,7 +317,7 @@ def cgh_direct_tiles():
         t = _Tile()
         _L().cgh_direct_tile_get(i, ctypes.byref(t))
         out.append((t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage,
-                    t.poly_pixels))
+                    t.poly_pixels, t.point_groups))
     return out
 
 
@@ -333,7 +335,8 @@ def cgh_tune(h, N: int, Nx: int, Ny: int, method="direct", stream=None):
     st = _L().cgh_tune(h, int(N), int(Nx), int(Ny), _method(method),
                       _stream_ptr(stream), ctypes.byref(t))
     _check(h, st, "cgh_tune")
-    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels)
+    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels,
+            t.point_groups)
 
 
 def cgh_last_device_status(h, stream=None) -> int:
@@ -347,7 +350,7 @@ def cgh_launch_count(h) -> int:
 
 KERNELS = {"prologue": 0, "direct_tables": 1, "direct": 2, "naive": 3,
            "sep_tables": 4, "gemm": 5, "bwd_direct": 6, "bwd_gemm": 7,
-           "bwd_reduce": 8, "batch": 9, "aux": 10}
+           "bwd_reduce": 8, "batch": 9, "aux": 10, "batch_sep": 11}
 
 
 def cgh_kernel_timing(h, enable: bool = True) -> None:

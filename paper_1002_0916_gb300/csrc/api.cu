@@ -452,6 +452,7 @@ cgh_status cgh_direct_tile_get(int i, cgh_direct_tile *out) {
     out->vec_y = t.vy;
     out->points_per_stage = t.pt;
     out->poly_pixels = t.np;
+    out->point_groups = t.g;
     return CGH_OK;
 }
 
@@ -462,11 +463,11 @@ cgh_status cgh_set_direct_tile(cgh_handle h, const cgh_direct_tile *tile) {
         return CGH_OK;
     }
     DirectTile t{tile->tile_x, tile->tile_y, tile->vec_x, tile->vec_y,
-                 tile->points_per_stage, tile->poly_pixels};
+                 tile->points_per_stage, tile->poly_pixels, tile->point_groups};
     int i = direct_tile_index(t);
     if (i < 0)
-        return h->fail(CGH_ERR_UNSUPPORTED, "tile %dx%d/%dx%d/%d/%d not compiled in",
-                       t.tx, t.ty, t.vx, t.vy, t.pt, t.np);
+        return h->fail(CGH_ERR_UNSUPPORTED, "tile %dx%d/%dx%d/%d/%d/%d not compiled in",
+                       t.tx, t.ty, t.vx, t.vy, t.pt, t.np, t.g);
     h->forced_tile = i;
     return CGH_OK;
 }

@@ -99,7 +99,7 @@ struct cgh_ctx {
     cgh_status run_batch_graph(uint64_t key, size_t meta_b, int nkernels,
                                const std::function<void(char *)> &fill_stage,
                                const std::function<cudaError_t(cudaStream_t)> &enqueue,
-                               cudaStream_t s);
+                               cudaStream_t s, int timer);
 
     void load_tune_cache();
     void release_all();

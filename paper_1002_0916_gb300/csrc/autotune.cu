@@ -77,19 +77,19 @@ void cgh_ctx::load_tune_cache() {
     char line[1024];
     while (fgets(line, sizeof(line), f)) {
         char dev[256] = {0}, bucket[128] = {0};
-        int tx, ty, vx, vy, pt, np;
-        // {"device": "...", "bucket": "...", "tile": [tx, ty, vx, vy, pt, np]}
+        int tx, ty, vx, vy, pt, np, g;
+        // {"device": "...", "bucket": "...", "tile": [tx, ty, vx, vy, pt, np, g]}
         const char *d = strstr(line, "\"device\": \"");
         const char *b = strstr(line, "\"bucket\": \"");
         const char *t = strstr(line, "\"tile\": [");
         if (!d || !b || !t) continue;
         if (sscanf(d + 11, "%255[^\"]", dev) != 1) continue;
         if (sscanf(b + 11, "%127[^\"]", bucket) != 1) continue;
-        if (sscanf(t + 9, "%d , %d , %d , %d , %d , %d", &tx, &ty, &vx, &vy, &pt,
-                   &np) != 6)
+        if (sscanf(t + 9, "%d , %d , %d , %d , %d , %d , %d", &tx, &ty, &vx, &vy,
+                   &pt, &np, &g) != 7)
             continue;
         if (strcmp(dev, device_name) != 0) continue;
-        int i = direct_tile_index(DirectTile{tx, ty, vx, vy, pt, np});
+        int i = direct_tile_index(DirectTile{tx, ty, vx, vy, pt, np, g});
         if (i >= 0) tuned[bucket] = i;
     }
     fclose(f);
@@ -164,14 +164,15 @@ extern "C" cgh_status cgh_tune(cgh_handle h, int N, int Nx, int Ny, int method,
             chosen->vec_y = t.vy;
             chosen->points_per_stage = t.pt;
             chosen->poly_pixels = t.np;
+            chosen->point_groups = t.g;
         }
         if (const char *path = cache_path()) {
             if (FILE *f = fopen(path, "a")) {
                 fprintf(f,
                         "{\"device\": \"%s\", \"bucket\": \"%s\", \"tile\": "
-                        "[%d, %d, %d, %d, %d, %d], \"ms\": %.5f}\n",
+                        "[%d, %d, %d, %d, %d, %d, %d], \"ms\": %.5f}\n",
                         h->device_name, b.c_str(), t.tx, t.ty, t.vx, t.vy, t.pt,
-                        t.np, best_ms);
+                        t.np, t.g, best_ms);
                 fclose(f);
             }
         }

@@ -62,12 +62,12 @@ __global__ void batch_tables_kernel(const BatchPrep *__restrict__ prep) {
                            b.phy, b.amp);
 }
 
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP>
-__global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST>::THREADS)
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
+__global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST, G>::THREADS)
 direct_batch_kernel(const BatchTile *__restrict__ probs,
                     const uint2 *__restrict__ items, int nitems,
                     unsigned *counter, unsigned *status) {
-    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP>;
+    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;
@@ -98,18 +98,18 @@ direct_batch_kernel(const BatchTile *__restrict__ probs,
                            status))
             return;
         g += (unsigned)ntile;
-        L::store(acc, xt, yt, bt.Nx, bt.Ny, bt.out, bt.vec_store);
+        L::store(acc, smem, xt, yt, bt.Nx, bt.Ny, bt.out, bt.vec_store);
     }
 }
 
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
 static cudaError_t launch_batch_t(const BatchTile *probs, const uint2 *items,
                                   int nitems, unsigned *counter, unsigned *status,
                                   int sm_count, cudaStream_t s) {
     // probs == nullptr: only set the kernel's attributes and cache its
     // occupancy (done before any capture)
-    using S = DirectShape<TX, TY, VX, VY, PT, NST>;
-    auto kern = direct_batch_kernel<TX, TY, VX, VY, PT, NST, NP>;
+    using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
+    auto kern = direct_batch_kernel<TX, TY, VX, VY, PT, NST, NP, G>;
     // attribute and occupancy once per device (no such calls inside a capture
     // of a geometry that has run before)
     static int per_sm_cache[64] = {};
@@ -137,11 +137,11 @@ static cudaError_t launch_batch(int tile_index, const BatchTile *probs,
                                 const uint2 *items, int nitems, unsigned *counter,
                                 unsigned *status, int sm_count, cudaStream_t s) {
     int i = 0;
-#define X(tx, ty, vx, vy, pt, ns, np)                                           \
+#define X(tx, ty, vx, vy, pt, ns, np, g)                                        \
     if (tile_index == i)                                                        \
-        return launch_batch_t<tx, ty, vx, vy, pt, ns, np>(probs, items, nitems,  \
-                                                          counter, status,      \
-                                                          sm_count, s);         \
+        return launch_batch_t<tx, ty, vx, vy, pt, ns, np, g>(probs, items, nitems, \
+                                                             counter, status,   \
+                                                             sm_count, s);      \
     ++i;
     CGH_DIRECT_TILES(X)
 #undef X
@@ -187,7 +187,7 @@ cgh_status cgh_ctx::ensure_host_stage(size_t bytes) {
 cgh_status cgh_ctx::run_batch_graph(uint64_t key, size_t meta_b, int nkernels,
                                     const std::function<void(char *)> &fill_stage,
                                     const std::function<cudaError_t(cudaStream_t)> &enqueue,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, int timer) {
     void *ptrs[4] = {bws.ptr, meta.ptr, host_stage, (void *)d_status};
     key = fnv1a(key, ptrs, sizeof(ptrs));
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -248,7 +248,7 @@ cgh_status cgh_ctx::run_batch_graph(uint64_t key, size_t meta_b, int nkernels,
         }
         batch_key = key;
     }
-    TimedLaunch tl(this, CGH_K_BATCH, s);
+    TimedLaunch tl(this, timer, s);
     e = cudaGraphLaunch(batch_exec, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     tl.done();
@@ -381,7 +381,7 @@ cgh_status cgh_ctx::batch_direct(const cgh_problem *probs, int count,
         return launch_batch(tile_index, d_tiles, d_items, nitems, counter, d_status,
                             sm_count, q);
     };
-    return run_batch_graph(key, meta_b, np ? 3 : 0, fill, enqueue, s);
+    return run_batch_graph(key, meta_b, np ? 3 : 0, fill, enqueue, s, CGH_K_BATCH);
 }
 
 cgh_status cgh_ctx::batch(const cgh_problem *probs, int count, int method,
@@ -480,6 +480,7 @@ extern "C" cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs,
             chosen->vec_y = t.vy;
             chosen->points_per_stage = t.pt;
             chosen->poly_pixels = t.np;
+            chosen->point_groups = t.g;
         }
     }
     if (prev != h->device) cudaSetDevice(prev);
@@ -634,5 +635,5 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
         if (r != cudaSuccess) return r;
         return launch_umma_grouped(d_gp, d_items, nitems, d_status, sm_count, q);
     };
-    return run_batch_graph(key, meta_b, np ? 3 : 0, fill, enqueue, s);
+    return run_batch_graph(key, meta_b, np ? 3 : 0, fill, enqueue, s, CGH_K_BATCH_SEP);
 }

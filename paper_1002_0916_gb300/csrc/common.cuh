@@ -128,7 +128,7 @@ __device__ __forceinline__ void set_status(unsigned *status, unsigned bits) {
 namespace cgh {
 
 struct DirectTile {
-    int tx, ty, vx, vy, pt, np;
+    int tx, ty, vx, vy, pt, np, g;
 };
 
 // Number of points after padding to a multiple of `pt`.

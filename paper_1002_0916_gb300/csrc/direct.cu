@@ -44,12 +44,12 @@ __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
 }
 
 // ------------------------------------------------------- direct kernel
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP>
-__global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST>::THREADS)
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
+__global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST, G>::THREADS)
 direct_fwd_kernel(const float *__restrict__ phx, const float *__restrict__ phy,
                   const float *__restrict__ amp, int Npad, int Nx, int Ny,
                   float *__restrict__ out, int vec_store, unsigned *status) {
-    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP>;
+    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;
@@ -71,7 +71,7 @@ direct_fwd_kernel(const float *__restrict__ phx, const float *__restrict__ phy,
                        phy + (size_t)yt * Npad * TY, amp, Npad / PT, 0u, acc,
                        status))
         return;
-    L::store(acc, xt, yt, Nx, Ny, out, vec_store);
+    L::store(acc, smem, xt, yt, Nx, Ny, out, vec_store);
 }
 
 // ------------------------------------------------------- naive kernel
@@ -95,7 +95,7 @@ __global__ void naive_fwd_kernel(const PointRec *__restrict__ rec, int N,
 // ------------------------------------------------------------ registry
 
 static const DirectTile kTiles[] = {
-#define X(tx, ty, vx, vy, pt, ns, np) {tx, ty, vx, vy, pt, np},
+#define X(tx, ty, vx, vy, pt, ns, np, g) {tx, ty, vx, vy, pt, np, g},
     CGH_DIRECT_TILES(X)
 #undef X
 };
@@ -106,7 +106,8 @@ DirectTile direct_tile_get(int i) { return kTiles[i]; }
 int direct_tile_index(const DirectTile &t) {
     for (int i = 0; i < kNumTiles; ++i)
         if (kTiles[i].tx == t.tx && kTiles[i].ty == t.ty && kTiles[i].vx == t.vx &&
-            kTiles[i].vy == t.vy && kTiles[i].pt == t.pt && kTiles[i].np == t.np)
+            kTiles[i].vy == t.vy && kTiles[i].pt == t.pt && kTiles[i].np == t.np &&
+            kTiles[i].g == t.g)
             return i;
     return -1;
 }
@@ -131,12 +132,12 @@ cudaError_t launch_direct_tables(const PointRec *rec, int Npad, int Nx, int Ny,
     return cudaGetLastError();
 }
 
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
 static cudaError_t launch_one(const float *phx, const float *phy,
                               const float *amp, int Npad, int Nx, int Ny,
                               float *out, unsigned *status, cudaStream_t s) {
-    using S = DirectShape<TX, TY, VX, VY, PT, NST>;
-    auto kern = direct_fwd_kernel<TX, TY, VX, VY, PT, NST, NP>;
+    using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
+    auto kern = direct_fwd_kernel<TX, TY, VX, VY, PT, NST, NP, G>;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -158,10 +159,11 @@ cudaError_t launch_direct_forward(int tile_index, const float *phx,
                                   int Nx, int Ny, float *out, unsigned *status,
                                   cudaStream_t s) {
     int i = 0;
-#define X(tx, ty, vx, vy, pt, ns, np)                                          \
+#define X(tx, ty, vx, vy, pt, ns, np, g)                                       \
     if (tile_index == i)                                                       \
-        return launch_one<tx, ty, vx, vy, pt, ns, np>(phx, phy, amp, Npad, Nx, \
-                                                      Ny, out, status, s);     \
+        return launch_one<tx, ty, vx, vy, pt, ns, np, g>(phx, phy, amp, Npad,  \
+                                                         Nx, Ny, out, status,  \
+                                                         s);                   \
     ++i;
     CGH_DIRECT_TILES(X)
 #undef X

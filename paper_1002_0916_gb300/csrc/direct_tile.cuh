@@ -8,20 +8,26 @@
 
 namespace cgh {
 
-// The tile shapes compiled in: X(TX, TY, VX, VY, PT, NST, NP) = pixels per
-// CTA along x and y, pixels per thread along x and y, points per
-// shared-memory stage, stages, and how many of each thread's VX * VY pixels
-// take the FMA-pipe cosine polynomial instead of the MUFU cosine (about a
-// quarter balances the two pipes).  Every shape has 256 threads per CTA.
-#define CGH_DIRECT_TILES(X)          \
-    X(64, 64, 4, 4, 32, 3, 4)        \
-    X(64, 64, 4, 4, 32, 3, 0)        \
-    X(64, 32, 4, 2, 32, 3, 2)        \
-    X(128, 32, 4, 4, 32, 3, 4)       \
-    X(32, 32, 2, 2, 64, 3, 1)        \
-    X(32, 32, 2, 2, 64, 3, 0)        \
-    X(128, 64, 8, 4, 16, 3, 8)       \
-    X(64, 16, 4, 1, 64, 3, 1)
+// The tile shapes compiled in: X(TX, TY, VX, VY, PT, NST, NP, G) = pixels
+// per CTA along x and y, pixels per thread along x and y, points per
+// shared-memory stage, stages, how many of each thread's VX * VY pixels take
+// the FMA-pipe cosine polynomial instead of the MUFU cosine (about a quarter
+// balances the two pipes), and G, the number of thread groups that split
+// each stage's points between them (their partial sums are added in a fixed
+// order at the end).  Every shape has 256 threads per CTA.
+#define CGH_DIRECT_TILES(X)             \
+    X(64, 64, 4, 4, 32, 3, 4, 1)        \
+    X(64, 64, 4, 4, 32, 3, 0, 1)        \
+    X(64, 32, 4, 2, 32, 3, 2, 1)        \
+    X(128, 32, 4, 4, 32, 3, 4, 1)       \
+    X(32, 32, 2, 2, 64, 3, 1, 1)        \
+    X(32, 32, 2, 2, 64, 3, 0, 1)        \
+    X(128, 64, 8, 4, 16, 3, 8, 1)       \
+    X(64, 16, 4, 1, 64, 3, 1, 1)        \
+    X(32, 32, 4, 4, 64, 3, 4, 4)        \
+    X(32, 32, 4, 4, 64, 3, 0, 4)        \
+    X(64, 32, 4, 4, 64, 3, 4, 2)        \
+    X(64, 64, 8, 4, 64, 3, 8, 2)
 
 // ------------------------------------------------------------- tables
 // Entries of the per-axis angle tables of one problem: x angles laid out
@@ -114,29 +120,33 @@ __device__ __forceinline__ float cos_poly(float th) {
     return p;
 }
 
-template <int TX, int TY, int VX, int VY, int PT, int NST>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int G = 1>
 struct DirectShape {
     static constexpr int NTX = TX / VX;
-    static constexpr int THREADS = NTX * (TY / VY);
-    static constexpr int SX = PT * TX;        // floats of x-angles per stage
-    static constexpr int SY = PT * TY;        // floats of y-angles per stage
-    static constexpr int SA = PT;             // amplitudes per stage
+    static constexpr int GT = NTX * (TY / VY);  // threads of one point group
+    static constexpr int THREADS = G * GT;
+    static constexpr int PG = PT / G;           // points per group per stage
+    static constexpr int SX = PT * TX;          // floats of x-angles per stage
+    static constexpr int SY = PT * TY;          // floats of y-angles per stage
+    static constexpr int SA = PT;               // amplitudes per stage
     static constexpr int STAGE = SX + SY + SA;
     static constexpr size_t SMEM = (size_t)NST * STAGE * sizeof(float);
     static_assert(TX % VX == 0 && TY % VY == 0, "tile not divisible");
     static_assert(PT % 4 == 0, "bulk copies need 16-byte multiples");
+    static_assert(PT % G == 0, "points of a stage split evenly over groups");
     static_assert((STAGE * 4) % 16 == 0, "stage alignment");
+    static_assert((size_t)(G - 1) * TX * TY <= (size_t)NST * STAGE,
+                  "partial sums of the extra groups fit in the stage ring");
 };
-
 
 // Per-CTA driver of the staged loop.  Point tile t of a pixel tile is the
 // (g0 + t)-th stage load of the CTA, so a persistent CTA can run many pixel
 // tiles back to back on the same NST-slot ring and mbarriers: slot
 // (g0 + t) % NST, barrier parity ((g0 + t) / NST) & 1.
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
 struct DirectTileLoop {
     static_assert(NP >= 0 && NP <= VX * VY, "polynomial pixels per thread");
-    using S = DirectShape<TX, TY, VX, VY, PT, NST>;
+    using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
 
     __device__ static void issue(float *smem, uint64_t *full, const float *gx,
                                  const float *gy, const float *amp, int t,
@@ -158,12 +168,14 @@ struct DirectTileLoop {
                                       float (&acc)[VY][VX], unsigned *status) {
         int issued = 0;  // meaningful in thread 0 only
         if (threadIdx.x == 0) {
+            fence_proxy_async_smem();  // the ring may hold partial sums
             for (int s = 0; s < NST && s < ntile; ++s) {
                 issue(smem, full, gx, gy, amp, s, (int)((g0 + s) % NST));
                 ++issued;
             }
         }
-        const int tx = threadIdx.x % S::NTX, ty = threadIdx.x / S::NTX;
+        const int lt = threadIdx.x % S::GT, grp = threadIdx.x / S::GT;
+        const int tx = lt % S::NTX, ty = lt / S::NTX;
         int t = 0;
         for (; t < ntile; ++t) {
             const unsigned g = g0 + (unsigned)t;
@@ -179,7 +191,7 @@ struct DirectTileLoop {
                 const float *sy = st + S::SX + ty * VY;
                 const float *sa = st + S::SX + S::SY;
 #pragma unroll 2
-                for (int q = 0; q < PT; ++q) {
+                for (int q = grp * S::PG; q < (grp + 1) * S::PG; ++q) {
                     const float a = sa[q];
                     float vx[VX], vy[VY];
                     VecLoad<VX>::ld(vx, sx + q * TX);
@@ -218,28 +230,58 @@ struct DirectTileLoop {
         return true;
     }
 
-    // Store the VX x VY pixels of this thread (pixel tile xt, yt).
-    __device__ static void store(const float (&acc)[VY][VX], int xt, int yt,
-                                 int Nx, int Ny, float *out, int vec_store) {
-        const int tx = threadIdx.x % S::NTX, ty = threadIdx.x / S::NTX;
-        const int x0 = xt * TX + tx * VX, y0 = yt * TY + ty * VY;
+    // Store the pixels of pixel tile (xt, yt).  With G > 1 the groups other
+    // than the first leave their partial sums in the (now idle) stage ring
+    // and the first group adds them in group order: deterministic.  Ends
+    // with the ring free for the next copies of a persistent CTA.
+    __device__ static void store(float (&acc)[VY][VX], float *smem, int xt,
+                                 int yt, int Nx, int Ny, float *out,
+                                 int vec_store) {
+        const int lt = threadIdx.x % S::GT, grp = threadIdx.x / S::GT;
+        const int tx = lt % S::NTX, ty = lt / S::NTX;
+        if (G > 1) {
+            if (grp > 0) {
+                float *part = smem + (size_t)(grp - 1) * TX * TY;
 #pragma unroll
-        for (int i = 0; i < VY; ++i) {
-            const int y = y0 + i;
-            if (y >= Ny) break;
-            float *orow = out + (size_t)y * Nx;
-            if (VX % 4 == 0 && vec_store && x0 + VX <= Nx) {
+                for (int i = 0; i < VY; ++i)
 #pragma unroll
-                for (int k = 0; k < VX; k += 4)
-                    *reinterpret_cast<float4 *>(orow + x0 + k) =
-                        make_float4(acc[i][k], acc[i][k + 1], acc[i][k + 2],
-                                    acc[i][k + 3]);
-            } else {
+                    for (int k = 0; k < VX; ++k)
+                        part[(ty * VY + i) * TX + tx * VX + k] = acc[i][k];
+            }
+            __syncthreads();
+            if (grp == 0) {
 #pragma unroll
-                for (int k = 0; k < VX; ++k)
-                    if (x0 + k < Nx) orow[x0 + k] = acc[i][k];
+                for (int g = 1; g < G; ++g) {
+                    const float *part = smem + (size_t)(g - 1) * TX * TY;
+#pragma unroll
+                    for (int i = 0; i < VY; ++i)
+#pragma unroll
+                        for (int k = 0; k < VX; ++k)
+                            acc[i][k] += part[(ty * VY + i) * TX + tx * VX + k];
+                }
             }
         }
+        if (grp == 0) {
+            const int x0 = xt * TX + tx * VX, y0 = yt * TY + ty * VY;
+#pragma unroll
+            for (int i = 0; i < VY; ++i) {
+                const int y = y0 + i;
+                if (y >= Ny) break;
+                float *orow = out + (size_t)y * Nx;
+                if (VX % 4 == 0 && vec_store && x0 + VX <= Nx) {
+#pragma unroll
+                    for (int k = 0; k < VX; k += 4)
+                        *reinterpret_cast<float4 *>(orow + x0 + k) =
+                            make_float4(acc[i][k], acc[i][k + 1], acc[i][k + 2],
+                                        acc[i][k + 3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < VX; ++k)
+                        if (x0 + k < Nx) orow[x0 + k] = acc[i][k];
+                }
+            }
+        }
+        if (G > 1) __syncthreads();
     }
 };
 

@@ -50,9 +50,9 @@ def test_status_strings(cg):
 def test_tile_registry(cg):
     tiles = cg.cgh_direct_tiles()
     assert len(tiles) >= 4
-    for tx, ty, vx, vy, pt, np_ in tiles:
-        assert tx % vx == 0 and ty % vy == 0 and pt % 4 == 0
-        assert (tx // vx) * (ty // vy) == 256 and 0 <= np_ <= vx * vy
+    for tx, ty, vx, vy, pt, np_, g in tiles:
+        assert tx % vx == 0 and ty % vy == 0 and pt % (4 * g) == 0
+        assert g * (tx // vx) * (ty // vy) == 256 and 0 <= np_ <= vx * vy
 
 
 def test_null_handle_is_rejected(cg):
