@@ -25,9 +25,12 @@
  *    streams at once: its workspace is shared between calls.
  *  * Argument errors are detected on the host and returned before any work
  *    is enqueued; outputs are untouched then.  Values that only the device
- *    sees (z_j <= 0, non-finite x_j, y_j, A_j, z_j) make the affected point
- *    contribute nothing and raise a bit in the handle's device status word,
- *    which cgh_last_device_status() reports.
+ *    sees (z_j <= 0, non-finite x_j, y_j, A_j, z_j, or z_j <= p^2/(2 lambda),
+ *    i.e. P_j >= 2 pi per pixel^2 -- tens of micrometres at visible
+ *    wavelengths and micrometre pitches, far inside the distance where the
+ *    Fresnel form holds) make the affected point contribute nothing and
+ *    raise a bit in the handle's device status word, which
+ *    cgh_last_device_status() reports.
  *  * The library never aborts the process, traps the GPU, or waits without
  *    a bound: every device-side wait gives up after about one second and
  *    records CGH_ERR_TIMEOUT in the device status word.
@@ -201,6 +204,8 @@ typedef struct {
                               the MUFU (special-function) unit     */
     int point_groups;      /* thread groups splitting each stage's
                               points (partial sums added in order) */
+    int packed;            /* 1: packed FP32x2 arithmetic on pixel
+                              pairs along x                        */
 } cgh_direct_tile;
 
 /* Number of direct-kernel tile shapes compiled into this build, and the
@@ -242,6 +247,12 @@ typedef enum {
  * CUDA events recorded on the launch's own stream; enable == 0: stop.  Both
  * reset the accumulated times. */
 cgh_status cgh_kernel_timing(cgh_handle h, int enable);
+
+/* As cgh_kernel_timing, but only the kernels whose bit (1 << cgh_kernel_id)
+ * is set in `mask` are bracketed (0: stop).  Events between two kernels
+ * order them fully, so leaving a kernel unbracketed keeps its launch
+ * overlapped with the kernel before it. */
+cgh_status cgh_kernel_timing_mask(cgh_handle h, uint32_t mask);
 
 /* Total device time (ms, from the events) and number of launches of kernel
  * `kernel` (a cgh_kernel_id) since timing was enabled.  Synchronises on the

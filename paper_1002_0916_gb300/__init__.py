@@ -28,6 +28,7 @@ __all__ = [
     "cgh_launch_count", "cgh_status_string", "cgh_last_error",
     "cgh_debug_gemm", "CGHFunction", "default_handle", "KERNELS",
     "cgh_kernel_timing", "cgh_kernel_time", "cgh_tune_batch",
+    "cgh_kernel_timing_mask",
 ]
 
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
@@ -52,7 +53,7 @@ class _Tile(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("vec_x", ctypes.c_int), ("vec_y", ctypes.c_int),
                 ("points_per_stage", ctypes.c_int), ("poly_pixels", ctypes.c_int),
-                ("point_groups", ctypes.c_int)]
+                ("point_groups", ctypes.c_int), ("packed", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -98,6 +99,8 @@ def _load():
     L.cgh_forward_noalloc.argtypes = [fp, fp, fp, ci, cd, cd, ci, ci, fp, vp]
     L.cgh_forward_noalloc.restype = ci
     L.cgh_kernel_timing.argtypes = [vp, ci]
+    L.cgh_kernel_timing_mask.argtypes = [vp, ctypes.c_uint32]
+    L.cgh_kernel_timing_mask.restype = ci
     L.cgh_kernel_time.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_uint64)]
     for name in ("cgh_create", "cgh_destroy", "cgh_forward", "cgh_forward_host",
@@ -307,7 +310,7 @@ def cgh_tune_batch(h, problems: Sequence[dict], method="direct", stream=None):
                              ctypes.byref(t))
     _check(h, st, "cgh_tune_batch")
     return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels,
-            t.point_groups)
+            t.point_groups, t.packed)
 
 
 # ---------------------------------------------------------- tiles/tuning
@@ -317,7 +320,7 @@ def cgh_direct_tiles():
         t = _Tile()
         _L().cgh_direct_tile_get(i, ctypes.byref(t))
         out.append((t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage,
-                    t.poly_pixels, t.point_groups))
+                    t.poly_pixels, t.point_groups, t.packed))
     return out
 
 
@@ -336,7 +339,7 @@ def cgh_tune(h, N: int, Nx: int, Ny: int, method="direct", stream=None):
                       _stream_ptr(stream), ctypes.byref(t))
     _check(h, st, "cgh_tune")
     return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels,
-            t.point_groups)
+            t.point_groups, t.packed)
 
 
 def cgh_last_device_status(h, stream=None) -> int:
@@ -357,6 +360,14 @@ def cgh_kernel_timing(h, enable: bool = True) -> None:
     """Bracket every kernel launch of ``h`` with CUDA events on its stream
     (resets the totals)."""
     _check(h, _L().cgh_kernel_timing(h, 1 if enable else 0), "cgh_kernel_timing")
+
+
+def cgh_kernel_timing_mask(h, kernels) -> None:
+    """Bracket only the named kernels (names or ids) with events."""
+    mask = 0
+    for k in kernels:
+        mask |= 1 << (KERNELS[k] if isinstance(k, str) else int(k))
+    _check(h, _L().cgh_kernel_timing_mask(h, mask), "cgh_kernel_timing_mask")
 
 
 def cgh_kernel_time(h, kernel):

@@ -409,10 +409,15 @@ cgh_status cgh_last_device_status(cgh_handle h, void *stream) {
 uint64_t cgh_launch_count(cgh_handle h) { return h ? h->launches : 0; }
 
 cgh_status cgh_kernel_timing(cgh_handle h, int enable) {
+    return cgh_kernel_timing_mask(h, enable ? 0xffffffffu : 0u);
+}
+
+cgh_status cgh_kernel_timing_mask(cgh_handle h, uint32_t mask) {
     if (!h) return CGH_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     h->timer_reset();
-    h->timing = enable != 0;
+    h->timing = mask != 0;
+    h->timing_mask = mask;
     return CGH_OK;
 }
 
@@ -453,6 +458,7 @@ cgh_status cgh_direct_tile_get(int i, cgh_direct_tile *out) {
     out->points_per_stage = t.pt;
     out->poly_pixels = t.np;
     out->point_groups = t.g;
+    out->packed = t.pk;
     return CGH_OK;
 }
 
@@ -463,11 +469,13 @@ cgh_status cgh_set_direct_tile(cgh_handle h, const cgh_direct_tile *tile) {
         return CGH_OK;
     }
     DirectTile t{tile->tile_x, tile->tile_y, tile->vec_x, tile->vec_y,
-                 tile->points_per_stage, tile->poly_pixels, tile->point_groups};
+                 tile->points_per_stage, tile->poly_pixels, tile->point_groups,
+                 tile->packed};
     int i = direct_tile_index(t);
     if (i < 0)
-        return h->fail(CGH_ERR_UNSUPPORTED, "tile %dx%d/%dx%d/%d/%d/%d not compiled in",
-                       t.tx, t.ty, t.vx, t.vy, t.pt, t.np, t.g);
+        return h->fail(CGH_ERR_UNSUPPORTED,
+                       "tile %dx%d/%dx%d/%d/%d/%d/%d not compiled in", t.tx, t.ty,
+                       t.vx, t.vy, t.pt, t.np, t.g, t.pk);
     h->forced_tile = i;
     return CGH_OK;
 }

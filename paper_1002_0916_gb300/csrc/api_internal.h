@@ -50,6 +50,7 @@ struct cgh_ctx {
 
     // kernel timing (cgh_kernel_timing / cgh_kernel_time)
     bool timing = false;
+    uint32_t timing_mask = 0;  // kernels (bit per cgh_kernel_id) to bracket
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[CGH_K_COUNT];
     std::vector<cudaEvent_t> event_pool;
     double kernel_ms[CGH_K_COUNT] = {0};
@@ -118,11 +119,13 @@ struct TimedLaunch {
     int kernel;
     cudaStream_t s;
     cudaEvent_t ev = nullptr;
-    TimedLaunch(cgh_ctx *h_, int k, cudaStream_t s_) : h(h_), kernel(k), s(s_) {
-        if (h->timing) h->timer_begin(kernel, s, &ev);
+    bool on;
+    TimedLaunch(cgh_ctx *h_, int k, cudaStream_t s_)
+        : h(h_), kernel(k), s(s_), on(h_->timing && ((h_->timing_mask >> k) & 1u)) {
+        if (on) h->timer_begin(kernel, s, &ev);
     }
     void done() {
         ++h->launches;
-        if (h->timing) h->timer_end(kernel, s, ev);
+        if (on) h->timer_end(kernel, s, ev);
     }
 };

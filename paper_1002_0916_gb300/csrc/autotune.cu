@@ -30,19 +30,24 @@ std::string size_bucket(int method, int N, int Nx, int Ny) {
 
 int default_direct_tile(int N, int Nx, int Ny, int sm_count) {
     (void)N;
-    const int resident = 3;  // CTAs of 256 threads per SM, typical
     double best = 1e300;
     int best_i = 0;
     for (int i = 0; i < direct_tile_count(); ++i) {
         DirectTile t = direct_tile_get(i);
+        // CTAs are handed to SMs as earlier ones finish, so an SM's share is
+        // about ceil(CTAs / SMs) CTAs of equal work
         long long ctas = (long long)((Nx + t.tx - 1) / t.tx) * ((Ny + t.ty - 1) / t.ty);
-        long long slots = (long long)sm_count * resident;
-        long long waves = (ctas + slots - 1) / slots;
-        // work per CTA, plus shared-memory loads per pixel update; moving a
-        // quarter of the cosines to the FMA pipe saves about a quarter
-        const double mufu_share = 1.0 - 0.75 * (double)t.np / (t.vx * t.vy);
-        double cost = (double)waves * t.tx * t.ty *
-                      (std::max(mufu_share, 0.76) + 0.25 / (t.vx * t.vy) + 0.25 / t.pt);
+        const double waves = (double)((ctas + sm_count - 1) / sm_count);
+        // Per-update cost model (in MUFU-cosine units), from the measured
+        // rates: a quarter of the cosines on the FMA pipe saves about a
+        // sixth, packed FP32x2 arithmetic a further ~7%, shared-memory loads
+        // (2 vectors + 1 broadcast per point per thread) cost in proportion
+        // to 1 / (pixels per thread).
+        const double share = (double)t.np / (t.vx * t.vy);
+        double per_pp = 1.0 - 0.65 * std::min(share, 0.25) + 0.3 * std::max(0.0, share - 0.25);
+        if (t.pk) per_pp *= 0.93;
+        per_pp += 0.5 / (t.vx * t.vy) + 0.25 / (t.pt / t.g);
+        const double cost = waves * t.tx * t.ty * per_pp;
         if (cost < best - 1e-9) {
             best = cost;
             best_i = i;
@@ -77,19 +82,19 @@ void cgh_ctx::load_tune_cache() {
     char line[1024];
     while (fgets(line, sizeof(line), f)) {
         char dev[256] = {0}, bucket[128] = {0};
-        int tx, ty, vx, vy, pt, np, g;
-        // {"device": "...", "bucket": "...", "tile": [tx, ty, vx, vy, pt, np, g]}
+        int tx, ty, vx, vy, pt, np, g, pk;
+        // {"device": "...", "bucket": "...", "tile": [tx, ty, vx, vy, pt, np, g, pk]}
         const char *d = strstr(line, "\"device\": \"");
         const char *b = strstr(line, "\"bucket\": \"");
         const char *t = strstr(line, "\"tile\": [");
         if (!d || !b || !t) continue;
         if (sscanf(d + 11, "%255[^\"]", dev) != 1) continue;
         if (sscanf(b + 11, "%127[^\"]", bucket) != 1) continue;
-        if (sscanf(t + 9, "%d , %d , %d , %d , %d , %d , %d", &tx, &ty, &vx, &vy,
-                   &pt, &np, &g) != 7)
+        if (sscanf(t + 9, "%d , %d , %d , %d , %d , %d , %d , %d", &tx, &ty, &vx,
+                   &vy, &pt, &np, &g, &pk) != 8)
             continue;
         if (strcmp(dev, device_name) != 0) continue;
-        int i = direct_tile_index(DirectTile{tx, ty, vx, vy, pt, np, g});
+        int i = direct_tile_index(DirectTile{tx, ty, vx, vy, pt, np, g, pk});
         if (i >= 0) tuned[bucket] = i;
     }
     fclose(f);
@@ -165,14 +170,15 @@ extern "C" cgh_status cgh_tune(cgh_handle h, int N, int Nx, int Ny, int method,
             chosen->points_per_stage = t.pt;
             chosen->poly_pixels = t.np;
             chosen->point_groups = t.g;
+            chosen->packed = t.pk;
         }
         if (const char *path = cache_path()) {
             if (FILE *f = fopen(path, "a")) {
                 fprintf(f,
                         "{\"device\": \"%s\", \"bucket\": \"%s\", \"tile\": "
-                        "[%d, %d, %d, %d, %d, %d, %d], \"ms\": %.5f}\n",
+                        "[%d, %d, %d, %d, %d, %d, %d, %d], \"ms\": %.5f}\n",
                         h->device_name, b.c_str(), t.tx, t.ty, t.vx, t.vy, t.pt,
-                        t.np, t.g, best_ms);
+                        t.np, t.g, t.pk, best_ms);
                 fclose(f);
             }
         }

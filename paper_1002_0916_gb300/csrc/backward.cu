@@ -101,27 +101,38 @@ __global__ void g_convert_kernel(const float *__restrict__ G, int Nx, int Ny,
 // Row 2j: cos th(u, j), row 2j+1: sin th(u, j), along u = 0..n-1, for the
 // x axis (U', n = Nx, row stride ldx) and the y axis (V', n = Ny, ldy).
 // FP16 hi and lo (scaled by 2^12) planes; rows of padding points are 0.
+// Grid: x over u in [0, Nx + Ny) (x coordinates, then y), y over groups of
+// AT_POINTS points from j0, whose records are staged in shared memory.
+constexpr int AT_POINTS = 16;
+
 __global__ void adj_tables_kernel(const PointRec *__restrict__ rec, int N,
-                                  int Npad, int Nx, int Ny, int ldx, int ldy,
-                                  __half *Uhi, __half *Ulo, __half *Vhi,
+                                  int Npad, int j0, int Nx, int Ny, int ldx,
+                                  int ldy, __half *Uhi, __half *Ulo, __half *Vhi,
                                   __half *Vlo) {
-    const long long total = (long long)Npad * (Nx + Ny);
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(e / (Nx + Ny));
-        const int r = (int)(e - (long long)j * (Nx + Ny));
-        const bool is_x = r < Nx;
-        const int u = is_x ? r : r - Nx;
+    __shared__ PointRec srec[AT_POINTS];
+    const int jb = j0 + (int)blockIdx.y * AT_POINTS;
+    if (threadIdx.x < AT_POINTS) {
+        const int j = jb + threadIdx.x;
+        srec[threadIdx.x] = j < N ? rec[j] : PointRec{};
+    }
+    __syncthreads();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= Nx + Ny) return;
+    const bool is_x = r < Nx;
+    const int u = is_x ? r : r - Nx;
+    __half *hi = is_x ? Uhi : Vhi;
+    __half *lo = is_x ? Ulo : Vlo;
+    const int ld = is_x ? ldx : ldy;
+    const int npts = Npad - jb < AT_POINTS ? Npad - jb : AT_POINTS;
+    for (int q = 0; q < npts; ++q) {
+        const int j = jb + q;
         float s = 0.0f, c = 0.0f;
         if (j < N) {
-            const PointRec pr = rec[j];
+            const PointRec &pr = srec[q];
             const uint64_t ph = is_x ? axis_phase(pr.c, pr.bx, pr.ax, u)
                                      : axis_phase(pr.c, pr.by, pr.ay, u);
-            sincospif(2.0f * (float)phase_hi(ph) * TURN_PER_U32, &s, &c);
+            __sincosf((float)phase_hi(ph) * RAD_PER_U32, &s, &c);
         }
-        __half *hi = is_x ? Uhi : Vhi;
-        __half *lo = is_x ? Ulo : Vlo;
-        const int ld = is_x ? ldx : ldy;
         const __half hc = __float2half_rn(c), hs = __float2half_rn(s);
         const size_t oc = (size_t)(2 * j) * ld + u, os = oc + ld;
         hi[oc] = hc;
@@ -327,12 +338,15 @@ static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
         }
         {
             TimedLaunch tl(h, CGH_K_SEP_TABLES, s);
-            const long long n = (long long)Npad * (Nx + Ny);
-            long long blocks = (n + 255) / 256;
-            if (blocks > 152 * 32) blocks = 152 * 32;
-            adj_tables_kernel<<<(int)blocks, 256, 0, s>>>(rec, N, Npad, Nx, Ny, ldx,
-                                                          ldy, Uhi, Ulo, Vhi, Vlo);
-            e = cudaGetLastError();
+            e = cudaSuccess;
+            const int span = 65535 * AT_POINTS;
+            for (int j0 = 0; j0 < Npad && e == cudaSuccess; j0 += span) {
+                const int nj = Npad - j0 < span ? Npad - j0 : span;
+                dim3 grid((Nx + Ny + 255) / 256, (nj + AT_POINTS - 1) / AT_POINTS);
+                adj_tables_kernel<<<grid, 256, 0, s>>>(rec, N, Npad, j0, Nx, Ny, ldx,
+                                                       ldy, Uhi, Ulo, Vhi, Vlo);
+                e = cudaGetLastError();
+            }
             if (e != cudaSuccess) return h->cuda_fail(e, "adjoint tables launch");
             tl.done();
         }

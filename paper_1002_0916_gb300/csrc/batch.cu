@@ -62,12 +62,12 @@ __global__ void batch_tables_kernel(const BatchPrep *__restrict__ prep) {
                            b.phy, b.amp);
 }
 
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G, int PK>
 __global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST, G>::THREADS)
 direct_batch_kernel(const BatchTile *__restrict__ probs,
                     const uint2 *__restrict__ items, int nitems,
                     unsigned *counter, unsigned *status) {
-    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G>;
+    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK != 0>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;
@@ -88,11 +88,8 @@ direct_batch_kernel(const BatchTile *__restrict__ probs,
         const BatchTile bt = probs[w.x];
         const int xt = (int)(w.y & 0xffffu), yt = (int)(w.y >> 16);
         const int ntile = bt.Npad / PT;
-        float acc[VY][VX];
-#pragma unroll
-        for (int i = 0; i < VY; ++i)
-#pragma unroll
-            for (int k = 0; k < VX; ++k) acc[i][k] = 0.0f;
+        typename L::Acc acc;
+        acc.zero();
         if (!L::accumulate(smem, full, &abort_flag, bt.phx + (size_t)xt * bt.Npad * TX,
                            bt.phy + (size_t)yt * bt.Npad * TY, bt.amp, ntile, g, acc,
                            status))
@@ -102,14 +99,14 @@ direct_batch_kernel(const BatchTile *__restrict__ probs,
     }
 }
 
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G, int PK>
 static cudaError_t launch_batch_t(const BatchTile *probs, const uint2 *items,
                                   int nitems, unsigned *counter, unsigned *status,
                                   int sm_count, cudaStream_t s) {
     // probs == nullptr: only set the kernel's attributes and cache its
     // occupancy (done before any capture)
     using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
-    auto kern = direct_batch_kernel<TX, TY, VX, VY, PT, NST, NP, G>;
+    auto kern = direct_batch_kernel<TX, TY, VX, VY, PT, NST, NP, G, PK>;
     // attribute and occupancy once per device (no such calls inside a capture
     // of a geometry that has run before)
     static int per_sm_cache[64] = {};
@@ -137,11 +134,10 @@ static cudaError_t launch_batch(int tile_index, const BatchTile *probs,
                                 const uint2 *items, int nitems, unsigned *counter,
                                 unsigned *status, int sm_count, cudaStream_t s) {
     int i = 0;
-#define X(tx, ty, vx, vy, pt, ns, np, g)                                        \
+#define X(tx, ty, vx, vy, pt, ns, np, g, pk)                                    \
     if (tile_index == i)                                                        \
-        return launch_batch_t<tx, ty, vx, vy, pt, ns, np, g>(probs, items, nitems, \
-                                                             counter, status,   \
-                                                             sm_count, s);      \
+        return launch_batch_t<tx, ty, vx, vy, pt, ns, np, g, pk>(                \
+            probs, items, nitems, counter, status, sm_count, s);                \
     ++i;
     CGH_DIRECT_TILES(X)
 #undef X
@@ -481,6 +477,7 @@ extern "C" cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs,
             chosen->points_per_stage = t.pt;
             chosen->poly_pixels = t.np;
             chosen->point_groups = t.g;
+            chosen->packed = t.pk;
         }
     }
     if (prev != h->device) cudaSetDevice(prev);

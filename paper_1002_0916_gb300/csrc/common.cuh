@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "cgh.h"
 
 namespace cgh {
@@ -122,13 +124,48 @@ __device__ __forceinline__ void set_status(unsigned *status, unsigned bits) {
     if (status) atomicOr(status, bits);
 }
 
+// Programmatic dependent launch: a kernel launched with
+// launch_dependent() may start while the previous kernel of the stream is
+// still running; it must call pdl_wait() before touching global memory that
+// kernel writes (a no-op for an ordinary launch).  pdl_trigger() lets the
+// next such kernel launch early.
+__device__ __forceinline__ void pdl_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+}  // namespace cgh
+
+// ------------------------------------------------ launch helper (host side)
+namespace cgh {
+
+// Launch `kern` on stream s as a programmatic dependent of the kernel
+// before it in the stream (see pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block,
+                             size_t smem, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 }  // namespace cgh
 
 // ------------------------------------------------ launchers (host side)
 namespace cgh {
 
 struct DirectTile {
-    int tx, ty, vx, vy, pt, np, g;
+    int tx, ty, vx, vy, pt, np, g, pk;
 };
 
 // Number of points after padding to a multiple of `pt`.

@@ -32,24 +32,54 @@
 namespace cgh {
 
 // ------------------------------------------------------------ tables
+// One block per DT_POINTS points (grid x) and 256 pixel columns/rows (grid
+// y) of the concatenated x and y ranges: the records are staged in shared
+// memory once, each thread then writes its coordinate for every point.
+constexpr int DT_POINTS = 16;
+
 __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
                                      int Npad, int TX, int TY, int nxt,
                                      int nyt, float *__restrict__ phx,
                                      float *__restrict__ phy,
                                      float *__restrict__ amp) {
-    const long long total = direct_table_entries(Npad, TX, TY, nxt, nyt);
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-         e < total; e += (long long)gridDim.x * blockDim.x)
-        direct_table_entry(rec, Npad, TX, TY, nxt, nyt, e, phx, phy, amp);
+    __shared__ PointRec srec[DT_POINTS];
+    pdl_wait();  // the records come from the kernel before
+    pdl_trigger();
+    const int j0 = blockIdx.x * DT_POINTS;
+    if (threadIdx.x < DT_POINTS && j0 + (int)threadIdx.x < Npad)
+        srec[threadIdx.x] = rec[j0 + threadIdx.x];
+    __syncthreads();
+    const int u = blockIdx.y * blockDim.x + threadIdx.x;
+    const int nx = nxt * TX, ny = nyt * TY;
+    const int npts = Npad - j0 < DT_POINTS ? Npad - j0 : DT_POINTS;
+    if (u < nx) {
+        const int t = u / TX, i = u - t * TX;
+        float *dst = phx + ((size_t)t * Npad + j0) * TX + i;
+        for (int q = 0; q < npts; ++q) {
+            const PointRec &r = srec[q];
+            dst[(size_t)q * TX] =
+                (float)phase_hi(axis_phase(r.c, r.bx, r.ax, u)) * RAD_PER_U32;
+        }
+    } else if (u < nx + ny) {
+        const int v = u - nx;
+        const int t = v / TY, i = v - t * TY;
+        float *dst = phy + ((size_t)t * Npad + j0) * TY + i;
+        for (int q = 0; q < npts; ++q) {
+            const PointRec &r = srec[q];
+            dst[(size_t)q * TY] =
+                (float)phase_hi(axis_phase(r.c, r.by, r.ay, v)) * RAD_PER_U32;
+        }
+    }
+    if (blockIdx.y == 0 && threadIdx.x < npts) amp[j0 + threadIdx.x] = srec[threadIdx.x].A;
 }
 
 // ------------------------------------------------------- direct kernel
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G, int PK>
 __global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST, G>::THREADS)
 direct_fwd_kernel(const float *__restrict__ phx, const float *__restrict__ phy,
                   const float *__restrict__ amp, int Npad, int Nx, int Ny,
                   float *__restrict__ out, int vec_store, unsigned *status) {
-    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G>;
+    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK != 0>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;
@@ -60,13 +90,11 @@ direct_fwd_kernel(const float *__restrict__ phx, const float *__restrict__ phy,
         for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
+    pdl_wait();  // the tables come from the kernel before
     __syncthreads();
 
-    float acc[VY][VX];
-#pragma unroll
-    for (int i = 0; i < VY; ++i)
-#pragma unroll
-        for (int k = 0; k < VX; ++k) acc[i][k] = 0.0f;
+    typename L::Acc acc;
+    acc.zero();
     if (!L::accumulate(smem, full, &abort_flag, phx + (size_t)xt * Npad * TX,
                        phy + (size_t)yt * Npad * TY, amp, Npad / PT, 0u, acc,
                        status))
@@ -95,7 +123,7 @@ __global__ void naive_fwd_kernel(const PointRec *__restrict__ rec, int N,
 // ------------------------------------------------------------ registry
 
 static const DirectTile kTiles[] = {
-#define X(tx, ty, vx, vy, pt, ns, np, g) {tx, ty, vx, vy, pt, np, g},
+#define X(tx, ty, vx, vy, pt, ns, np, g, pk) {tx, ty, vx, vy, pt, np, g, pk},
     CGH_DIRECT_TILES(X)
 #undef X
 };
@@ -107,7 +135,7 @@ int direct_tile_index(const DirectTile &t) {
     for (int i = 0; i < kNumTiles; ++i)
         if (kTiles[i].tx == t.tx && kTiles[i].ty == t.ty && kTiles[i].vx == t.vx &&
             kTiles[i].vy == t.vy && kTiles[i].pt == t.pt && kTiles[i].np == t.np &&
-            kTiles[i].g == t.g)
+            kTiles[i].g == t.g && kTiles[i].pk == t.pk)
             return i;
     return -1;
 }
@@ -122,22 +150,18 @@ cudaError_t launch_direct_tables(const PointRec *rec, int Npad, int Nx, int Ny,
                                  const DirectTile &t, float *phx, float *phy,
                                  float *amp, cudaStream_t s) {
     int nxt = (Nx + t.tx - 1) / t.tx, nyt = (Ny + t.ty - 1) / t.ty;
-    long long total = (long long)nxt * Npad * t.tx + (long long)nyt * Npad * t.ty + Npad;
-    int threads = 256;
-    long long blocks = (total + threads - 1) / threads;
-    if (blocks > 152LL * 16) blocks = 152LL * 16;
-    direct_tables_kernel<<<(int)blocks, threads, 0, s>>>(rec, Npad, t.tx, t.ty,
-                                                          nxt, nyt, phx, phy,
-                                                          amp);
-    return cudaGetLastError();
+    const int span = nxt * t.tx + nyt * t.ty;  // <= 65536 + 2 tiles
+    dim3 grid((Npad + DT_POINTS - 1) / DT_POINTS, (span + 255) / 256);
+    return launch_dependent(direct_tables_kernel, grid, dim3(256), 0, s, rec, Npad,
+                            t.tx, t.ty, nxt, nyt, phx, phy, amp);
 }
 
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G, int PK>
 static cudaError_t launch_one(const float *phx, const float *phy,
                               const float *amp, int Npad, int Nx, int Ny,
                               float *out, unsigned *status, cudaStream_t s) {
     using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
-    auto kern = direct_fwd_kernel<TX, TY, VX, VY, PT, NST, NP, G>;
+    auto kern = direct_fwd_kernel<TX, TY, VX, VY, PT, NST, NP, G, PK>;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -149,9 +173,8 @@ static cudaError_t launch_one(const float *phx, const float *phy,
     }
     dim3 grid((Nx + TX - 1) / TX, (Ny + TY - 1) / TY);
     int vec_store = (Nx % 4 == 0) && (((uintptr_t)out & 15) == 0);
-    kern<<<grid, S::THREADS, S::SMEM, s>>>(phx, phy, amp, Npad, Nx, Ny, out,
-                                          vec_store, status);
-    return cudaGetLastError();
+    return launch_dependent(kern, grid, dim3(S::THREADS), S::SMEM, s, phx, phy, amp,
+                            Npad, Nx, Ny, out, vec_store, status);
 }
 
 cudaError_t launch_direct_forward(int tile_index, const float *phx,
@@ -159,11 +182,11 @@ cudaError_t launch_direct_forward(int tile_index, const float *phx,
                                   int Nx, int Ny, float *out, unsigned *status,
                                   cudaStream_t s) {
     int i = 0;
-#define X(tx, ty, vx, vy, pt, ns, np, g)                                       \
+#define X(tx, ty, vx, vy, pt, ns, np, g, pk)                                   \
     if (tile_index == i)                                                       \
-        return launch_one<tx, ty, vx, vy, pt, ns, np, g>(phx, phy, amp, Npad,  \
-                                                         Nx, Ny, out, status,  \
-                                                         s);                   \
+        return launch_one<tx, ty, vx, vy, pt, ns, np, g, pk>(phx, phy, amp,    \
+                                                             Npad, Nx, Ny,     \
+                                                             out, status, s);  \
     ++i;
     CGH_DIRECT_TILES(X)
 #undef X

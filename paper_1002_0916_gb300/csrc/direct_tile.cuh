@@ -12,22 +12,28 @@ namespace cgh {
 // per CTA along x and y, pixels per thread along x and y, points per
 // shared-memory stage, stages, how many of each thread's VX * VY pixels take
 // the FMA-pipe cosine polynomial instead of the MUFU cosine (about a quarter
-// balances the two pipes), and G, the number of thread groups that split
+// balances the two pipes), G, the number of thread groups that split
 // each stage's points between them (their partial sums are added in a fixed
-// order at the end).  Every shape has 256 threads per CTA.
-#define CGH_DIRECT_TILES(X)             \
-    X(64, 64, 4, 4, 32, 3, 4, 1)        \
-    X(64, 64, 4, 4, 32, 3, 0, 1)        \
-    X(64, 32, 4, 2, 32, 3, 2, 1)        \
-    X(128, 32, 4, 4, 32, 3, 4, 1)       \
-    X(32, 32, 2, 2, 64, 3, 1, 1)        \
-    X(32, 32, 2, 2, 64, 3, 0, 1)        \
-    X(128, 64, 8, 4, 16, 3, 8, 1)       \
-    X(64, 16, 4, 1, 64, 3, 1, 1)        \
-    X(32, 32, 4, 4, 64, 3, 4, 4)        \
-    X(32, 32, 4, 4, 64, 3, 0, 4)        \
-    X(64, 32, 4, 4, 64, 3, 4, 2)        \
-    X(64, 64, 8, 4, 64, 3, 8, 2)
+// order at the end), and PK = 1 for packed FP32x2 arithmetic on pixel pairs
+// along x (half the issue slots for the adds and FMAs).  Every shape has 256
+// threads per CTA.
+#define CGH_DIRECT_TILES(X)                \
+    X(64, 64, 4, 4, 32, 3, 4, 1, 0)        \
+    X(64, 64, 4, 4, 32, 3, 0, 1, 0)        \
+    X(64, 32, 4, 2, 32, 3, 2, 1, 0)        \
+    X(128, 32, 4, 4, 32, 3, 4, 1, 0)       \
+    X(32, 32, 2, 2, 64, 3, 1, 1, 0)        \
+    X(32, 32, 2, 2, 64, 3, 0, 1, 0)        \
+    X(128, 64, 8, 4, 16, 3, 8, 1, 0)       \
+    X(64, 16, 4, 1, 64, 3, 1, 1, 0)        \
+    X(32, 32, 4, 4, 64, 3, 4, 4, 0)        \
+    X(32, 32, 4, 4, 64, 3, 0, 4, 0)        \
+    X(64, 32, 4, 4, 64, 3, 4, 2, 0)        \
+    X(64, 64, 8, 4, 64, 3, 8, 2, 0)        \
+    X(32, 32, 4, 4, 64, 3, 4, 4, 1)        \
+    X(32, 32, 4, 4, 64, 3, 6, 4, 1)        \
+    X(64, 32, 4, 4, 64, 3, 6, 2, 1)        \
+    X(64, 64, 8, 4, 64, 3, 10, 2, 1)
 
 // ------------------------------------------------------------- tables
 // Entries of the per-axis angle tables of one problem: x angles laid out
@@ -102,14 +108,15 @@ struct VecLoad<8> {
     }
 };
 
-// cos(theta) for |theta| < 2 pi on the FMA pipe: fold to
-// d = min(|theta|, 2 pi - |theta|) in [0, pi] (cos is even and 2 pi
-// periodic), then the degree-6 polynomial in d^2 of cos_poly.h (max error
-// about 6e-7, like the hardware cosine's 2^-21.4 on [-pi, pi]).
-__device__ __forceinline__ float cos_poly(float th) {
-    const float a = fabsf(th);
-    const float d = fminf(a, 6.28318530717958647692f - a);
-    const float s = d * d;
+// cos(theta) for |theta| < 2 pi on the FMA pipe: with u = |theta| - pi in
+// [-pi, pi), cos(theta) = cos(|theta|) = -cos(u), and cos(u) is the degree-6
+// polynomial in u^2 of cos_poly.h (max error about 6e-7, like the hardware
+// cosine's 2^-21.4 on [-pi, pi]).  The caller folds the sign into A.
+constexpr float PI_F = 3.14159265358979323846f;
+
+__device__ __forceinline__ float neg_cos_poly(float th) {
+    const float u = fabsf(th) - PI_F;
+    const float s = u * u;
     float p = COS_C6;
     p = fmaf(p, s, COS_C5);
     p = fmaf(p, s, COS_C4);
@@ -117,8 +124,57 @@ __device__ __forceinline__ float cos_poly(float th) {
     p = fmaf(p, s, COS_C2);
     p = fmaf(p, s, COS_C1);
     p = fmaf(p, s, COS_C0);
-    return p;
+    return p;  // = -cos(th)
 }
+
+// The same for two angles at once with packed FP32x2 arithmetic.
+__device__ __forceinline__ float2 neg_cos_poly2(float2 th) {
+    const float2 u = make_float2(fabsf(th.x) - PI_F, fabsf(th.y) - PI_F);
+    const float2 s = __fmul2_rn(u, u);
+    float2 p = make_float2(COS_C6, COS_C6);
+    p = __ffma2_rn(p, s, make_float2(COS_C5, COS_C5));
+    p = __ffma2_rn(p, s, make_float2(COS_C4, COS_C4));
+    p = __ffma2_rn(p, s, make_float2(COS_C3, COS_C3));
+    p = __ffma2_rn(p, s, make_float2(COS_C2, COS_C2));
+    p = __ffma2_rn(p, s, make_float2(COS_C1, COS_C1));
+    p = __ffma2_rn(p, s, make_float2(COS_C0, COS_C0));
+    return p;  // = (-cos(th.x), -cos(th.y))
+}
+
+// Per-thread accumulators: VY x VX floats, or VY x VX/2 packed pairs.
+template <int VY, int VX, bool PK>
+struct DirectAcc {
+    float v[VY][VX];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < VY; ++i)
+#pragma unroll
+            for (int k = 0; k < VX; ++k) v[i][k] = 0.0f;
+    }
+    __device__ __forceinline__ float get(int i, int k) const { return v[i][k]; }
+    __device__ __forceinline__ void add(int i, int k, float x) { v[i][k] += x; }
+};
+
+template <int VY, int VX>
+struct DirectAcc<VY, VX, true> {
+    static_assert(VX % 2 == 0, "packed pairs along x");
+    float2 v[VY][VX / 2];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < VY; ++i)
+#pragma unroll
+            for (int k = 0; k < VX / 2; ++k) v[i][k] = make_float2(0.0f, 0.0f);
+    }
+    __device__ __forceinline__ float get(int i, int k) const {
+        return (k & 1) ? v[i][k >> 1].y : v[i][k >> 1].x;
+    }
+    __device__ __forceinline__ void add(int i, int k, float x) {
+        if (k & 1)
+            v[i][k >> 1].y += x;
+        else
+            v[i][k >> 1].x += x;
+    }
+};
 
 template <int TX, int TY, int VX, int VY, int PT, int NST, int G = 1>
 struct DirectShape {
@@ -143,10 +199,13 @@ struct DirectShape {
 // (g0 + t)-th stage load of the CTA, so a persistent CTA can run many pixel
 // tiles back to back on the same NST-slot ring and mbarriers: slot
 // (g0 + t) % NST, barrier parity ((g0 + t) / NST) & 1.
-template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G>
+template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G,
+          bool PK>
 struct DirectTileLoop {
     static_assert(NP >= 0 && NP <= VX * VY, "polynomial pixels per thread");
+    static_assert(!PK || NP % 2 == 0, "packed pairs take the polynomial together");
     using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
+    using Acc = DirectAcc<VY, VX, PK>;
 
     __device__ static void issue(float *smem, uint64_t *full, const float *gx,
                                  const float *gy, const float *amp, int t,
@@ -164,8 +223,8 @@ struct DirectTileLoop {
     __device__ static bool accumulate(float *smem, uint64_t *full,
                                       volatile int *abort_flag, const float *gx,
                                       const float *gy, const float *amp,
-                                      int ntile, unsigned g0,
-                                      float (&acc)[VY][VX], unsigned *status) {
+                                      int ntile, unsigned g0, Acc &acc,
+                                      unsigned *status) {
         int issued = 0;  // meaningful in thread 0 only
         if (threadIdx.x == 0) {
             fence_proxy_async_smem();  // the ring may hold partial sums
@@ -196,16 +255,38 @@ struct DirectTileLoop {
                     float vx[VX], vy[VY];
                     VecLoad<VX>::ld(vx, sx + q * TX);
                     VecLoad<VY>::ld(vy, sy + q * TY);
+                    // the first NP pixels of the thread take the FMA-pipe
+                    // polynomial, the rest the MUFU cosine (compile-time split)
+                    if constexpr (PK) {
+                        const float2 a2 = make_float2(a, a), na2 = make_float2(-a, -a);
 #pragma unroll
-                    for (int i = 0; i < VY; ++i)
+                        for (int i = 0; i < VY; ++i) {
+                            const float2 y2 = make_float2(vy[i], vy[i]);
 #pragma unroll
-                        for (int k = 0; k < VX; ++k) {
-                            const float th = vx[k] + vy[i];
-                            // the first NP pixels of the thread on the FMA
-                            // pipe, the rest on the MUFU (compile-time split)
-                            const float cs = (i * VX + k < NP) ? cos_poly(th) : __cosf(th);
-                            acc[i][k] = fmaf(a, cs, acc[i][k]);
+                            for (int k = 0; k < VX; k += 2) {
+                                const float2 th =
+                                    __fadd2_rn(make_float2(vx[k], vx[k + 1]), y2);
+                                float2 &ac = acc.v[i][k >> 1];
+                                if (i * VX + k < NP)
+                                    ac = __ffma2_rn(na2, neg_cos_poly2(th), ac);
+                                else
+                                    ac = __ffma2_rn(
+                                        a2, make_float2(__cosf(th.x), __cosf(th.y)), ac);
+                            }
                         }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < VY; ++i)
+#pragma unroll
+                            for (int k = 0; k < VX; ++k) {
+                                const float th = vx[k] + vy[i];
+                                float &ac = acc.v[i][k];
+                                if (i * VX + k < NP)
+                                    ac = fmaf(-a, neg_cos_poly(th), ac);
+                                else
+                                    ac = fmaf(a, __cosf(th), ac);
+                            }
+                    }
                 }
             }
             __syncthreads();  // every thread is done with slot s
@@ -234,9 +315,8 @@ struct DirectTileLoop {
     // than the first leave their partial sums in the (now idle) stage ring
     // and the first group adds them in group order: deterministic.  Ends
     // with the ring free for the next copies of a persistent CTA.
-    __device__ static void store(float (&acc)[VY][VX], float *smem, int xt,
-                                 int yt, int Nx, int Ny, float *out,
-                                 int vec_store) {
+    __device__ static void store(Acc &acc, float *smem, int xt, int yt, int Nx,
+                                 int Ny, float *out, int vec_store) {
         const int lt = threadIdx.x % S::GT, grp = threadIdx.x / S::GT;
         const int tx = lt % S::NTX, ty = lt / S::NTX;
         if (G > 1) {
@@ -246,7 +326,7 @@ struct DirectTileLoop {
                 for (int i = 0; i < VY; ++i)
 #pragma unroll
                     for (int k = 0; k < VX; ++k)
-                        part[(ty * VY + i) * TX + tx * VX + k] = acc[i][k];
+                        part[(ty * VY + i) * TX + tx * VX + k] = acc.get(i, k);
             }
             __syncthreads();
             if (grp == 0) {
@@ -257,7 +337,7 @@ struct DirectTileLoop {
                     for (int i = 0; i < VY; ++i)
 #pragma unroll
                         for (int k = 0; k < VX; ++k)
-                            acc[i][k] += part[(ty * VY + i) * TX + tx * VX + k];
+                            acc.add(i, k, part[(ty * VY + i) * TX + tx * VX + k]);
                 }
             }
         }
@@ -272,12 +352,12 @@ struct DirectTileLoop {
 #pragma unroll
                     for (int k = 0; k < VX; k += 4)
                         *reinterpret_cast<float4 *>(orow + x0 + k) =
-                            make_float4(acc[i][k], acc[i][k + 1], acc[i][k + 2],
-                                        acc[i][k + 3]);
+                            make_float4(acc.get(i, k), acc.get(i, k + 1),
+                                        acc.get(i, k + 2), acc.get(i, k + 3));
                 } else {
 #pragma unroll
                     for (int k = 0; k < VX; ++k)
-                        if (x0 + k < Nx) orow[x0 + k] = acc[i][k];
+                        if (x0 + k < Nx) orow[x0 + k] = acc.get(i, k);
                 }
             }
         }

@@ -18,8 +18,38 @@ __device__ __forceinline__ uint64_t to_fix64(double f) {
 
 __device__ __forceinline__ double frac(double v) { return v - floor(v); }
 
+// |x| = m 2^-s exactly, with m a 24-bit integer (frexpf) and s an integer
+// shift (negative for |x| >= 2^24).
+__device__ __forceinline__ void float_mant_shift(float x, uint64_t &m, int &s) {
+    const float ax = fabsf(x);
+    if (ax == 0.0f) {
+        m = 0;
+        s = 0;
+        return;
+    }
+    int e;
+    const float f = frexpf(ax, &e);          // ax = f 2^e, f in [1/2, 1)
+    m = (uint64_t)(f * 16777216.0f);         // exact: 24 significant bits
+    s = 24 - e;
+}
+
+// (c v) 2^-s modulo 2^64 from the 128-bit product (bits below 2^0 dropped).
+__device__ __forceinline__ uint64_t mul_shift(uint64_t c, uint64_t v, int s) {
+    const uint64_t lo = c * v, hi = __umul64hi(c, v);
+    if (s <= 0) return s > -64 ? lo << (-s) : 0;
+    if (s < 64) return (hi << (64 - s)) | (lo >> s);
+    if (s < 128) return hi >> (s - 64);
+    return 0;
+}
+
 // Record of point j (all zero for padding points j >= N and for rejected
-// points: z <= 0 or a non-finite value, which also raise DEV_BAD_POINT).
+// points, which also raise DEV_BAD_POINT: z <= 0, a non-finite value, or
+// z_j <= p^2 / (2 lambda), i.e. Q_j >= 1 turn per pixel^2, far inside the
+// distance where the Fresnel form of Eq. 1 holds).
+//
+// Only Q_j itself is computed in FP64.  With c = Q_j in 0.64 fixed point
+// and u_j = m 2^-s exactly, the axis coefficients are exact integer
+// arithmetic on c: b = 2 c u_j and a = c u_j^2 (mod 1 turn).
 __device__ __forceinline__ PointRec make_point_rec(const float *points,
                                                    const float *A,
                                                    const float *z, int N, int j,
@@ -30,18 +60,23 @@ __device__ __forceinline__ PointRec make_point_rec(const float *points,
     r.A = 0.0f;
     r.Q32 = 0.0f;
     if (j < N) {
-        float xj = points[2 * j], yj = points[2 * j + 1];
-        float aj = A[j], zj = z[j];
-        bool ok = isfinite(xj) && isfinite(yj) && isfinite(aj) &&
-                  isfinite(zj) && zj > 0.0f;
+        const float xj = points[2 * j], yj = points[2 * j + 1];
+        const float aj = A[j], zj = z[j];
+        const double Q = (p * p) / (2.0 * lambda * (double)zj);
+        const bool ok = isfinite(xj) && isfinite(yj) && isfinite(aj) &&
+                        isfinite(zj) && zj > 0.0f && Q < 1.0;
         if (ok) {
-            double Q = (p * p) / (2.0 * lambda * (double)zj);
-            double x = (double)xj, y = (double)yj;
-            r.c = to_fix64(frac(Q));
-            r.bx = to_fix64(frac(2.0 * Q * x));
-            r.ax = to_fix64(frac(Q * x * x));
-            r.by = to_fix64(frac(2.0 * Q * y));
-            r.ay = to_fix64(frac(Q * y * y));
+            r.c = to_fix64(Q);
+            uint64_t m;
+            int s;
+            float_mant_shift(xj, m, s);
+            uint64_t b = mul_shift(r.c, m, s) << 1;
+            r.bx = xj < 0.0f ? (uint64_t)0 - b : b;
+            r.ax = mul_shift(r.c, m * m, 2 * s);
+            float_mant_shift(yj, m, s);
+            b = mul_shift(r.c, m, s) << 1;
+            r.by = yj < 0.0f ? (uint64_t)0 - b : b;
+            r.ay = mul_shift(r.c, m * m, 2 * s);
             r.A = aj;
             r.Q32 = (float)Q;
         } else {

@@ -2,12 +2,12 @@
 //
 // For each object point j (Section 1, Eq. 1; P_j = pi p^2 / (lambda z_j)):
 //   Q_j = P_j / (2 pi) = p^2 / (2 lambda z_j)     [turns per pixel^2]
-//   c   = frac(Q_j),  b = frac(2 Q_j u_j),  a = frac(Q_j u_j^2)  per axis u
-// in FP64, each converted to unsigned 0.64 fixed-point turns.  Then the axis
-// phase c u^2 - b u + a (mod 1) equals Q_j (u - u_j)^2 (mod 1) for integer u,
-// evaluated without rounding in 64-bit integer arithmetic.  The only
-// rounding left is FP64's in Q_j, b and a (relative 2^-53 of Q_j u_j^2,
-// about 1e-13 turns at 3840 x 2160).
+// in FP64, stored as c = Q_j in unsigned 0.64 fixed-point turns; then per
+// axis u the coefficients b = 2 Q_j u_j and a = Q_j u_j^2 (mod 1) in exact
+// integer arithmetic on c (u_j is a float, i.e. an integer times a power of
+// two).  The axis phase c u^2 - b u + a (mod 1) equals Q_j (u - u_j)^2
+// (mod 1) for integer u, evaluated without rounding in 64-bit integer
+// arithmetic; the only rounding is Q_j's own (FP64, then 2^-64).
 #include <math.h>
 
 #include "common.cuh"
@@ -21,6 +21,7 @@ __global__ void prologue_kernel(const float *__restrict__ points,
                                 double lambda, double p,
                                 PointRec *__restrict__ rec,
                                 unsigned *status) {
+    pdl_trigger();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Npad) return;
     rec[j] = make_point_rec(points, A, z, N, j, lambda, p, status);
@@ -31,7 +32,9 @@ cudaError_t launch_prologue(const float *points, const float *A,
                             double p, PointRec *rec, unsigned *status,
                             cudaStream_t s) {
     if (Npad <= 0) return cudaSuccess;
-    int threads = 128;
+    // FP64 runs at a few operations per clock per SM on this GPU, so spread
+    // the points thinly over many SMs
+    int threads = 32;
     int blocks = (Npad + threads - 1) / threads;
     prologue_kernel<<<blocks, threads, 0, s>>>(points, A, z, N, Npad, lambda,
                                                 p, rec, status);

@@ -29,34 +29,48 @@
 
 namespace cgh {
 
+// Grid: x over points j (256 per block), y over groups of ST_ROWS table
+// rows from row0; each thread loads its point's record once.
+constexpr int ST_ROWS = 8;
+
 template <int KIND>
 __global__ void sep_tables_kernel(const PointRec *__restrict__ rec, int N,
-                                  int Npad, int Nx, int Ny, int Kp,
+                                  int Nx, int Ny, int Kp, int row0,
                                   void *__restrict__ Lhi, void *__restrict__ Llo,
                                   void *__restrict__ Rhi,
                                   void *__restrict__ Rlo) {
-    const long long total = (long long)(Nx + Ny) * (Kp / 2);
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x)
-        sep_table_entry<KIND>(rec, N, Nx, Kp, e, Lhi, Llo, Rhi, Rlo);
+    pdl_wait();  // the records come from the kernel before
+    pdl_trigger();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= Kp / 2) return;
+    const int r0 = row0 + (int)blockIdx.y * ST_ROWS;
+    const int r1 = r0 + ST_ROWS < Nx + Ny ? r0 + ST_ROWS : Nx + Ny;
+    const PointRec pr = j < N ? rec[j] : PointRec{};
+    for (int r = r0; r < r1; ++r)
+        sep_table_entry_rj<KIND>(pr, j < N, Nx, Kp, r, j, Lhi, Llo, Rhi, Rlo);
 }
 
 cudaError_t launch_sep_tables(const PointRec *rec, int N, int Npad, int Nx,
                               int Ny, int Kp, int kind, void *Lhi, void *Llo,
                               void *Rhi, void *Rlo, cudaStream_t s) {
-    const long long total = (long long)(Nx + Ny) * (Kp / 2);
-    const int threads = 256;
-    long long blocks = (total + threads - 1) / threads;
-    if (blocks > 152LL * 32) blocks = 152LL * 32;
-    if (kind == 0)
-        sep_tables_kernel<0><<<(int)blocks, threads, 0, s>>>(rec, N, Npad, Nx, Ny,
-                                                             Kp, Lhi, Llo, Rhi, Rlo);
-    else if (kind == 1)
-        sep_tables_kernel<1><<<(int)blocks, threads, 0, s>>>(rec, N, Npad, Nx, Ny,
-                                                             Kp, Lhi, Llo, Rhi, Rlo);
-    else
-        sep_tables_kernel<2><<<(int)blocks, threads, 0, s>>>(rec, N, Npad, Nx, Ny,
-                                                             Kp, Lhi, Llo, Rhi, Rlo);
+    (void)Npad;
+    // row groups in launches of at most 65535 (the grid's y limit)
+    const int rows = Nx + Ny;
+    for (int row0 = 0; row0 < rows; row0 += 65535 * ST_ROWS) {
+        const int n = rows - row0 < 65535 * ST_ROWS ? rows - row0 : 65535 * ST_ROWS;
+        dim3 grid((Kp / 2 + 255) / 256, (n + ST_ROWS - 1) / ST_ROWS);
+        cudaError_t e;
+        if (kind == 0)
+            e = launch_dependent(sep_tables_kernel<0>, grid, dim3(256), 0, s, rec, N,
+                                 Nx, Ny, Kp, row0, Lhi, Llo, Rhi, Rlo);
+        else if (kind == 1)
+            e = launch_dependent(sep_tables_kernel<1>, grid, dim3(256), 0, s, rec, N,
+                                 Nx, Ny, Kp, row0, Lhi, Llo, Rhi, Rlo);
+        else
+            e = launch_dependent(sep_tables_kernel<2>, grid, dim3(256), 0, s, rec, N,
+                                 Nx, Ny, Kp, row0, Lhi, Llo, Rhi, Rlo);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 

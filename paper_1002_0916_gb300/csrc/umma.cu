@@ -179,6 +179,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
         umma::tmem_alloc(&tmem_base, S::TMEM_COLS);
         umma::tmem_relinquish();
     }
+    pdl_wait();  // operands come from the kernel before
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
@@ -367,8 +368,8 @@ static cudaError_t launch_gemm_t(const GemmOperands &op, const AdjEpiArgs &ea,
     GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status};
     dim3 grid((op.N + BN - 1) / BN, (op.M + S::BM - 1) / S::BM);
     const uint32_t idesc = umma::idesc_f16(S::BM, BN, op.bf16);
-    kern<<<grid, 192, S::SMEM, s>>>(tA, tB, tA2, tB2, g, ea, idesc);
-    return cudaGetLastError();
+    return launch_dependent(kern, grid, dim3(192), S::SMEM, s, tA, tB, tA2, tB2, g,
+                            ea, idesc);
 }
 
 bool gemm_operands_ok(const GemmOperands &op) {

@@ -17,15 +17,15 @@ def _coeffs():
 
 
 def _kernel_cos(theta):
-    """The kernel's fold and Horner evaluation, in float32."""
+    """The kernel's fold (u = |theta| - pi, cos theta = -cos u) and Horner
+    evaluation, in float32."""
     c = _coeffs()
-    a = np.abs(theta.astype(np.float32))
-    d = np.minimum(a, np.float32(6.28318530717958647692) - a)
-    s = (d * d).astype(np.float32)
+    u = (np.abs(theta.astype(np.float32)) - np.float32(np.pi)).astype(np.float32)
+    s = (u * u).astype(np.float32)
     p = np.full_like(s, c[-1])
     for k in range(len(c) - 2, -1, -1):
         p = (p * s + c[k]).astype(np.float32)
-    return p
+    return -p
 
 
 def test_polynomial_error_bound():
