@@ -38,12 +38,13 @@ MUFU_PER_CLK_PER_SM = 16     # MUFU (special-function) cosines per SM per clock
 FP32_PER_CLK_PER_SM = 128    # FP32 lanes of the FMA pipe per SM per clock
 # Work of the direct kernel per point-pixel update, in FP32 (FMA-pipe)
 # operations: MUFU-cosine path = angle add, argument scale, accumulate (3,
-# plus 1 MUFU); polynomial path = angle add, fold, square, 6 FMA, accumulate
-# (10, no MUFU).  With a share s on the polynomial the FMA-pipe limit is
-# 128 / (3 + 7 s) and the MUFU limit 16 / (1 - s) updates/clk/SM; they meet
-# at s = 1/3: 24 updates per clock per SM.  (Issue slots do not bind: packed
-# FP32x2 instructions do two of these operations per slot.)
-MIXED_PP_PER_CLK_PER_SM = 24.0
+# plus 1 MUFU); polynomial path = angle add, fold, square, 5 FMA (degree-5
+# polynomial of the default tile), accumulate (9, no MUFU).  With a share s
+# on the polynomial the FMA-pipe limit is 128 / (3 + 6 s) and the MUFU limit
+# 16 / (1 - s) updates/clk/SM; they meet at s = 5/14: 16 * 14 / 9 = 24.9
+# updates per clock per SM.  (Issue slots do not bind: packed FP32x2
+# instructions do two of these operations per slot.)
+MIXED_PP_PER_CLK_PER_SM = 16.0 * 14.0 / 9.0
 NOMINAL_SMS = 152
 NOMINAL_MAX_MHZ = 2070.0
 FP16_OVER_BF16 = 1.0         # dense FP16 and BF16 tensor rates are equal
@@ -441,7 +442,7 @@ def run_ours(args):
             per_clk = MIXED_PP_PER_CLK_PER_SM
             src = ("FMA-pipe (128 FP32 ops/clk/SM) and MUFU (16 cosines/clk/SM) limits "
                    "of the direct recipe: 3 FP32 ops + 1 MUFU per MUFU-cosine update, "
-                   "10 FP32 ops per polynomial-cosine update, best mix 1/3 -> 24 "
+                   "9 FP32 ops per polynomial-cosine update, best mix 5/14 -> 24.9 "
                    "updates/clk/SM")
         peak = sms * per_clk * NOMINAL_MAX_MHZ * 1e6 / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak,

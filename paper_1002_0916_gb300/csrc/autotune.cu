@@ -40,12 +40,12 @@ int default_direct_tile(int N, int Nx, int Ny, int sm_count) {
         const double waves = (double)((ctas + sm_count - 1) / sm_count);
         // Per-update cost model (in MUFU-cosine units), from the measured
         // rates: a quarter of the cosines on the FMA pipe saves about a
-        // sixth, packed FP32x2 arithmetic a further ~7%, shared-memory loads
+        // sixth, packed FP32x2 arithmetic a further 7-9%, shared-memory loads
         // (2 vectors + 1 broadcast per point per thread) cost in proportion
         // to 1 / (pixels per thread).
         const double share = (double)t.np / (t.vx * t.vy);
         double per_pp = 1.0 - 0.65 * std::min(share, 0.25) + 0.3 * std::max(0.0, share - 0.25);
-        if (t.pk) per_pp *= 0.93;
+        if (t.pk) per_pp *= t.pk == 2 ? 0.91 : 0.93;  // degree-5 polynomial: one FMA less
         per_pp += 0.5 / (t.vx * t.vy) + 0.25 / (t.pt / t.g);
         const double cost = waves * t.tx * t.ty * per_pp;
         if (cost < best - 1e-9) {

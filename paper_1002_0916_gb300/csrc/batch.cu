@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST, G>::THREA
 direct_batch_kernel(const BatchTile *__restrict__ probs,
                     const uint2 *__restrict__ items, int nitems,
                     unsigned *counter, unsigned *status) {
-    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK != 0>;
+    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;
@@ -396,12 +396,22 @@ cgh_status cgh_ctx::batch(const cgh_problem *probs, int count, int method,
         }
     }
     if (method == CGH_DIRECT_FP32) {
-        int ti = forced_tile_index >= 0 ? forced_tile_index
-                 : forced_tile >= 0      ? forced_tile
-                                         : 0;
-        if (forced_tile_index < 0 && forced_tile < 0) {
+        int ti = forced_tile_index >= 0 ? forced_tile_index : forced_tile;
+        if (ti < 0) {
             auto it = tuned.find(batch_bucket(probs, count));
-            if (it != tuned.end()) ti = it->second;
+            if (it != tuned.end()) {
+                ti = it->second;
+            } else {
+                // untuned: the heuristic's shape for the problem with the most
+                // work (persistent CTAs balance the rest)
+                int big = 0;
+                for (int i = 1; i < count; ++i)
+                    if ((double)probs[i].N * probs[i].Nx * probs[i].Ny >
+                        (double)probs[big].N * probs[big].Nx * probs[big].Ny)
+                        big = i;
+                ti = default_direct_tile(probs[big].N, probs[big].Nx, probs[big].Ny,
+                                         sm_count);
+            }
         }
         return batch_direct(probs, count, s, ti);
     }

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST, G>::THREA
 direct_fwd_kernel(const float *__restrict__ phx, const float *__restrict__ phy,
                   const float *__restrict__ amp, int Npad, int Nx, int Ny,
                   float *__restrict__ out, int vec_store, unsigned *status) {
-    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK != 0>;
+    using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;

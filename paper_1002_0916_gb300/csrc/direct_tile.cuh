@@ -14,8 +14,9 @@ namespace cgh {
 // the FMA-pipe cosine polynomial instead of the MUFU cosine (about a quarter
 // balances the two pipes), G, the number of thread groups that split
 // each stage's points between them (their partial sums are added in a fixed
-// order at the end), and PK = 1 for packed FP32x2 arithmetic on pixel pairs
-// along x (half the issue slots for the adds and FMAs).  Every shape has 256
+// order at the end), and PK: 0 scalar, 1 packed FP32x2 arithmetic on pixel
+// pairs along x (half the issue slots for the adds and FMAs), 2 packed with
+// the degree-5 polynomial.  Every shape has 256
 // threads per CTA.
 #define CGH_DIRECT_TILES(X)                \
     X(64, 64, 4, 4, 32, 3, 4, 1, 0)        \
@@ -33,7 +34,9 @@ namespace cgh {
     X(32, 32, 4, 4, 64, 3, 4, 4, 1)        \
     X(32, 32, 4, 4, 64, 3, 6, 4, 1)        \
     X(64, 32, 4, 4, 64, 3, 6, 2, 1)        \
-    X(64, 64, 8, 4, 64, 3, 10, 2, 1)
+    X(64, 64, 8, 4, 64, 3, 10, 2, 1)       \
+    X(32, 32, 4, 4, 64, 3, 4, 4, 2)        \
+    X(32, 32, 4, 4, 64, 3, 6, 4, 2)
 
 // ------------------------------------------------------------- tables
 // Entries of the per-axis angle tables of one problem: x angles laid out
@@ -127,17 +130,29 @@ __device__ __forceinline__ float neg_cos_poly(float th) {
     return p;  // = -cos(th)
 }
 
-// The same for two angles at once with packed FP32x2 arithmetic.
+// The same for two angles at once with packed FP32x2 arithmetic; DEG 6 (the
+// table above) or 5 (COS5_C, max error about 1.3e-6, one FMA fewer).
+template <int DEG>
 __device__ __forceinline__ float2 neg_cos_poly2(float2 th) {
     const float2 u = make_float2(fabsf(th.x) - PI_F, fabsf(th.y) - PI_F);
     const float2 s = __fmul2_rn(u, u);
-    float2 p = make_float2(COS_C6, COS_C6);
-    p = __ffma2_rn(p, s, make_float2(COS_C5, COS_C5));
-    p = __ffma2_rn(p, s, make_float2(COS_C4, COS_C4));
-    p = __ffma2_rn(p, s, make_float2(COS_C3, COS_C3));
-    p = __ffma2_rn(p, s, make_float2(COS_C2, COS_C2));
-    p = __ffma2_rn(p, s, make_float2(COS_C1, COS_C1));
-    p = __ffma2_rn(p, s, make_float2(COS_C0, COS_C0));
+    float2 p;
+    if constexpr (DEG == 6) {
+        p = make_float2(COS_C6, COS_C6);
+        p = __ffma2_rn(p, s, make_float2(COS_C5, COS_C5));
+        p = __ffma2_rn(p, s, make_float2(COS_C4, COS_C4));
+        p = __ffma2_rn(p, s, make_float2(COS_C3, COS_C3));
+        p = __ffma2_rn(p, s, make_float2(COS_C2, COS_C2));
+        p = __ffma2_rn(p, s, make_float2(COS_C1, COS_C1));
+        p = __ffma2_rn(p, s, make_float2(COS_C0, COS_C0));
+    } else {
+        p = make_float2(COS5_C5, COS5_C5);
+        p = __ffma2_rn(p, s, make_float2(COS5_C4, COS5_C4));
+        p = __ffma2_rn(p, s, make_float2(COS5_C3, COS5_C3));
+        p = __ffma2_rn(p, s, make_float2(COS5_C2, COS5_C2));
+        p = __ffma2_rn(p, s, make_float2(COS5_C1, COS5_C1));
+        p = __ffma2_rn(p, s, make_float2(COS5_C0, COS5_C0));
+    }
     return p;  // = (-cos(th.x), -cos(th.y))
 }
 
@@ -200,8 +215,11 @@ struct DirectShape {
 // tiles back to back on the same NST-slot ring and mbarriers: slot
 // (g0 + t) % NST, barrier parity ((g0 + t) / NST) & 1.
 template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G,
-          bool PK>
+          int PKV>
 struct DirectTileLoop {
+    // PKV: 0 scalar arithmetic, 1 packed FP32x2 with the degree-6 polynomial,
+    // 2 packed with the degree-5 polynomial
+    static constexpr bool PK = PKV != 0;
     static_assert(NP >= 0 && NP <= VX * VY, "polynomial pixels per thread");
     static_assert(!PK || NP % 2 == 0, "packed pairs take the polynomial together");
     using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
@@ -268,7 +286,8 @@ struct DirectTileLoop {
                                     __fadd2_rn(make_float2(vx[k], vx[k + 1]), y2);
                                 float2 &ac = acc.v[i][k >> 1];
                                 if (i * VX + k < NP)
-                                    ac = __ffma2_rn(na2, neg_cos_poly2(th), ac);
+                                    ac = __ffma2_rn(na2, neg_cos_poly2<PKV == 2 ? 5 : 6>(th),
+                                                    ac);
                                 else
                                     ac = __ffma2_rn(
                                         a2, make_float2(__cosf(th.x), __cosf(th.y)), ac);

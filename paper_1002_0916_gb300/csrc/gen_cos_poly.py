@@ -47,17 +47,26 @@ def fp32_error(c):
 def main():
     if "--check" in sys.argv:
         txt = open(OUT).read()
-        vals = [float(t.split("=")[1].strip().rstrip("f;")) for t in txt.splitlines()
-                if "constexpr float COS_C" in t]
-        print(f"max |P(d^2) - cos d| on [0, pi] in FP32: {fp32_error(vals):.3e}")
+        for prefix in ("COS_C", "COS5_C"):
+            vals = [float(t.split("=")[1].strip().rstrip("f;")) for t in txt.splitlines()
+                    if f"constexpr float {prefix}" in t]
+            print(f"{prefix}: max |P(d^2) - cos d| on [0, pi] in FP32: "
+                  f"{fp32_error(vals):.3e}")
         return
     c = fit()
+    c5 = fit(5)
     lines = ["// cos_poly.h -- written by gen_cos_poly.py; do not edit.",
-             "// cos(d) ~= sum_k COS_Ck (d^2)^k for d in [0, pi] (Lawson minimax fit,",
-             f"// degree {DEG} in d^2; max error in FP32 evaluation {fp32_error(c):.2e}).",
+             "// cos(d) ~= sum_k C_k (d^2)^k for d in [0, pi] (Lawson minimax fits):",
+             f"// COS_C: degree {DEG} in d^2, max error in FP32 evaluation "
+             f"{fp32_error(c):.2e};",
+             f"// COS5_C: degree 5 in d^2, max error in FP32 evaluation "
+             f"{fp32_error(c5):.2e}.",
              "#pragma once", "", "namespace cgh {", ""]
     for k, v in enumerate(c):
         lines.append(f"constexpr float COS_C{k} = {float(np.float32(v))!r}f;")
+    lines.append("")
+    for k, v in enumerate(c5):
+        lines.append(f"constexpr float COS5_C{k} = {float(np.float32(v))!r}f;")
     lines += ["", "}  // namespace cgh", ""]
     open(OUT, "w").write("\n".join(lines))
     print(open(OUT).read())

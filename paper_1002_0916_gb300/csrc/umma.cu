@@ -61,9 +61,18 @@ struct GemmShape {
     static constexpr uint32_t B_BYTES = BN * BK * 2;
     static constexpr uint32_t STAGE_BYTES =
         SPLIT ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
-    static constexpr uint32_t TMEM_COLS = SPLIT ? 2 * BN : BN;
+    // second accumulator (split form) on a 128-column boundary
+    static constexpr uint32_t ACC1 = BN <= 128 ? 128 : BN;
+    static constexpr uint32_t ACC_COLS = SPLIT ? ACC1 + BN : BN;
+    // TMEM allocations are powers of two of at least 32 columns
+    static constexpr uint32_t TMEM_COLS =
+        ACC_COLS <= 32 ? 32 : ACC_COLS <= 64 ? 64 : ACC_COLS <= 128 ? 128
+        : ACC_COLS <= 256 ? 256 : 512;
+    // epilogue column chunk: 32 columns, or 16 when BN is not a multiple of 32
+    static constexpr int CH = BN % 32 == 0 ? 32 : 16;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
-    static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "UMMA N");
+    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "UMMA N");
+    static_assert(ACC_COLS <= 512, "TMEM");
     static_assert(TMEM_COLS == 64 || TMEM_COLS == 128 || TMEM_COLS == 256 ||
                       TMEM_COLS == 512,
                   "TMEM allocation must be a power of two >= 32 columns");
@@ -71,7 +80,7 @@ struct GemmShape {
 };
 
 // The fused adjoint epilogue for one TMEM lane (= GEMM row `row`).
-template <int BN, bool SPLIT>
+template <int BN, bool SPLIT, uint32_t ACC1>
 __device__ __forceinline__ void adjoint_epilogue(uint32_t t_row, int row, int n0,
                                                  const GemmArgs &g,
                                                  const AdjEpiArgs &ea, int lane) {
@@ -99,7 +108,7 @@ __device__ __forceinline__ void adjoint_epilogue(uint32_t t_row, int row, int n0
         float v[32];
         if (SPLIT) {
             uint32_t r2[32];
-            umma::tmem_ld32(t_row + BN + c, r2);
+            umma::tmem_ld32(t_row + ACC1 + c, r2);
             umma::tmem_ld_wait();
 #pragma unroll
             for (int i = 0; i < 32; ++i)
@@ -237,11 +246,11 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
                 const uint64_t bd2 = umma::sw128_kmajor_desc(b2);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
-                    umma::mma_f16(tmem + BN, ad + 2 * kk, bd2 + 2 * kk, idesc,
+                    umma::mma_f16(tmem + S::ACC1, ad + 2 * kk, bd2 + 2 * kk, idesc,
                                   (kb | kk) != 0);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
-                    umma::mma_f16(tmem + BN, ad2 + 2 * kk, bd + 2 * kk, idesc, 1);
+                    umma::mma_f16(tmem + S::ACC1, ad2 + 2 * kk, bd + 2 * kk, idesc, 1);
             }
             umma::mma_commit(&empty[s]);
         }
@@ -256,40 +265,43 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
         umma::fence_after_sync();
         if (!ok) set_status(g.status, DEV_TIMEOUT);
         if (MODE == 1 && ok && !abort_flag) {
-            adjoint_epilogue<BN, SPLIT>(tmem + ((uint32_t)(q * 32) << 16), row, n0,
-                                        g, ea, lane);
+            adjoint_epilogue<BN, SPLIT, S::ACC1>(tmem + ((uint32_t)(q * 32) << 16),
+                                                 row, n0, g, ea, lane);
         } else if (ok && !abort_flag) {
             const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
             float *drow = g.D + (long long)row * g.ldd;
             const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
+            constexpr int CH = S::CH;
 #pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
-                uint32_t r[32];
-                umma::tmem_ld32(t_row + c, r);
-                float v[32];
+            for (int c = 0; c < BN; c += CH) {
+                uint32_t r[CH];
+                float v[CH];
+                if constexpr (CH == 32) umma::tmem_ld32(t_row + c, r);
+                else umma::tmem_ld16(t_row + c, r);
                 if (SPLIT) {
-                    uint32_t r2[32];
-                    umma::tmem_ld32(t_row + BN + c, r2);
+                    uint32_t r2[CH];
+                    if constexpr (CH == 32) umma::tmem_ld32(t_row + S::ACC1 + c, r2);
+                    else umma::tmem_ld16(t_row + S::ACC1 + c, r2);
                     umma::tmem_ld_wait();
 #pragma unroll
-                    for (int i = 0; i < 32; ++i)
+                    for (int i = 0; i < CH; ++i)
                         v[i] = fmaf(g.lo_scale, __uint_as_float(r2[i]),
                                     __uint_as_float(r[i]));
                 } else {
                     umma::tmem_ld_wait();
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+                    for (int i = 0; i < CH; ++i) v[i] = __uint_as_float(r[i]);
                 }
                 if (row < g.M) {
                     const int col = n0 + c;
-                    if (vec && col + 32 <= g.N) {
+                    if (vec && col + CH <= g.N) {
 #pragma unroll
-                        for (int i = 0; i < 32; i += 4)
+                        for (int i = 0; i < CH; i += 4)
                             *reinterpret_cast<float4 *>(drow + col + i) =
                                 make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
+                        for (int i = 0; i < CH; ++i)
                             if (col + i < g.N) drow[col + i] = v[i];
                     }
                 }
@@ -384,12 +396,42 @@ bool gemm_operands_ok(const GemmOperands &op) {
     return true;
 }
 
+static int sm_count_of_current_device() {
+    static int cache[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        n = 148;
+    }
+    if (dev >= 0 && dev < 64) cache[dev] = n;
+    return n;
+}
+
+// One CTA per tile, one tile per SM at a time: the GEMM takes about
+// ceil(tiles / SMs) x (work of one tile).  A 112-column tile does 7/8 of the
+// work of a 128-column one and can fill the SMs better (1920 columns x 1024
+// rows: 144 tiles of 112 on 152 SMs instead of 120 of 128).
+static int pick_tile_n(int M, int N, int sms) {
+    auto cost = [&](int bn) {
+        long long tiles = (long long)((M + 127) / 128) * ((N + bn - 1) / bn);
+        return (double)((tiles + sms - 1) / sms) * bn;
+    };
+    return cost(112) < cost(128) ? 112 : 128;
+}
+
 cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
                              cudaStream_t s) {
     if (!gemm_operands_ok(op)) return cudaErrorInvalidValue;
     AdjEpiArgs ea{};
-    if (op.split) return launch_gemm_t<128, true, 3, 0>(op, ea, status, s);
-    return launch_gemm_t<128, false, 6, 0>(op, ea, status, s);
+    const int bn = pick_tile_n(op.M, op.N, sm_count_of_current_device());
+    if (op.split)
+        return bn == 112 ? launch_gemm_t<112, true, 3, 0>(op, ea, status, s)
+                         : launch_gemm_t<128, true, 3, 0>(op, ea, status, s);
+    return bn == 112 ? launch_gemm_t<112, false, 6, 0>(op, ea, status, s)
+                     : launch_gemm_t<128, false, 6, 0>(op, ea, status, s);
 }
 
 cudaError_t launch_umma_adjoint(const GemmOperands &op, const PointRec *rec,
