@@ -36,7 +36,8 @@ namespace cgh {
     X(64, 32, 4, 4, 64, 3, 6, 2, 1)        \
     X(64, 64, 8, 4, 64, 3, 10, 2, 1)       \
     X(32, 32, 4, 4, 64, 3, 4, 4, 2)        \
-    X(32, 32, 4, 4, 64, 3, 6, 4, 2)
+    X(32, 32, 4, 4, 64, 3, 6, 4, 2)        \
+    X(32, 32, 4, 4, 32, 3, 4, 4, 2)
 
 // ------------------------------------------------------------- tables
 // Entries of the per-axis angle tables of one problem: x angles laid out
