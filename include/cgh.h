@@ -204,8 +204,10 @@ typedef struct {
                               the MUFU (special-function) unit     */
     int point_groups;      /* thread groups splitting each stage's
                               points (partial sums added in order) */
-    int packed;            /* 1: packed FP32x2 arithmetic on pixel
-                              pairs along x                        */
+    int packed;            /* 0: scalar FP32; 1: packed FP32x2
+                              arithmetic on pixel pairs along x,
+                              degree-6 polynomial; 2: packed,
+                              degree-5 polynomial                  */
 } cgh_direct_tile;
 
 /* Number of direct-kernel tile shapes compiled into this build, and the
