@@ -210,6 +210,30 @@ typedef struct {
                               degree-5 polynomial                  */
 } cgh_direct_tile;
 
+/* How the direct kernel spreads its pixel tiles over the SMs (a scheduling
+ * choice of this implementation; the paper launches one work group per
+ * 16 x 16 pixel block, Section 2.1).
+ *   CGH_SCHED_GRID:  one CTA per pixel tile.  When the tile count is not a
+ *                    multiple of the SM count the last wave leaves SMs idle.
+ *   CGH_SCHED_SPLIT: one CTA per pixel tile, except for the last
+ *                    (tiles mod SMs) tiles: their points are cut into chunks
+ *                    of point stages, one CTA per chunk, run at the end of
+ *                    the grid; each such tile is the sum of its chunks'
+ *                    partial tiles added in chunk order (deterministic; the
+ *                    rounding differs from GRID's by the summation order
+ *                    only).
+ *   CGH_SCHED_AUTO:  SPLIT (the default).
+ * The batch entry point (cgh_batch) has its own persistent schedule. */
+typedef enum {
+    CGH_SCHED_AUTO = 0,
+    CGH_SCHED_GRID = 1,
+    CGH_SCHED_SPLIT = 2
+} cgh_direct_schedule;
+
+/* Select the direct kernel's schedule for later calls on this handle.
+ * CGH_ERR_INVALID_ARG for a null handle or an unknown value. */
+cgh_status cgh_set_direct_schedule(cgh_handle h, int schedule);
+
 /* Number of direct-kernel tile shapes compiled into this build, and the
  * i-th of them (0 <= i < count). */
 int cgh_direct_tile_count(void);

@@ -82,6 +82,7 @@ def _load():
     L.cgh_direct_tile_count.argtypes = []
     L.cgh_direct_tile_get.argtypes = [ci, ctypes.POINTER(_Tile)]
     L.cgh_set_direct_tile.argtypes = [vp, ctypes.POINTER(_Tile)]
+    L.cgh_set_direct_schedule.argtypes = [vp, ci]
     L.cgh_tune.argtypes = [vp, ci, ci, ci, ci, vp, ctypes.POINTER(_Tile)]
     L.cgh_tune_batch.argtypes = [vp, ctypes.POINTER(_Problem), ci, ci, vp,
                                  ctypes.POINTER(_Tile)]
@@ -331,6 +332,17 @@ def cgh_set_direct_tile(h, tile=None):
         t = _Tile(*tile)
         st = _L().cgh_set_direct_tile(h, ctypes.byref(t))
     _check(h, st, "cgh_set_direct_tile")
+
+
+SCHEDULES = {"auto": 0, "grid": 1, "split": 2}
+
+
+def cgh_set_direct_schedule(h, schedule="auto"):
+    """How the direct kernel spreads pixel tiles over the SMs: "grid" (one
+    CTA per tile), "split" (persistent CTAs with equal runs of (tile, point
+    stage) units, split tiles summed in a fixed order) or "auto"."""
+    st = _L().cgh_set_direct_schedule(h, SCHEDULES[schedule])
+    _check(h, st, "cgh_set_direct_schedule")
 
 
 def cgh_tune(h, N: int, Nx: int, Ny: int, method="direct", stream=None):

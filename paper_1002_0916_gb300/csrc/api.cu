@@ -122,14 +122,25 @@ cgh_status cgh_ctx::forward_direct(const float *points, const float *A,
     const size_t tab_f = direct_phase_table_floats(t, Npad, Nx, Ny);
     const size_t tab_b = align256(tab_f * sizeof(float));
     const size_t amp_b = align256((size_t)Npad * sizeof(float));
-    cgh_status st = ensure(ws, rec_b + tab_b + amp_b, s, "direct workspace");
+    const int nxt = (Nx + t.tx - 1) / t.tx;
+    // schedule: one CTA per tile, with the tail tiles split into point
+    // chunks when the tiles do not spread evenly over the SMs
+    const DirectSplit d = direct_split_plan(tile_index, sm_count, Npad, Nx, Ny,
+                                            direct_schedule != CGH_SCHED_GRID);
+    const int nsplit = d.tiles - d.tail;
+    const size_t part_b = align256((size_t)d.chunks() * t.tx * t.ty * sizeof(float));
+    const size_t cnt_b = align256((size_t)nsplit * sizeof(unsigned));
+    cgh_status st = ensure(ws, rec_b + tab_b + amp_b + part_b + cnt_b, s,
+                           "direct workspace");
     if (st) return st;
     char *base = (char *)ws.ptr;
     PointRec *rec = (PointRec *)base;
-    int nxt = (Nx + t.tx - 1) / t.tx;
     float *phx = (float *)(base + rec_b);
     float *phy = phx + (size_t)nxt * Npad * t.tx;
     float *amp = (float *)(base + rec_b + tab_b);
+    float *part = nsplit ? (float *)(base + rec_b + tab_b + amp_b) : nullptr;
+    unsigned *count =
+        nsplit ? (unsigned *)(base + rec_b + tab_b + amp_b + part_b) : nullptr;
 
     {
         TimedLaunch tl(this, CGH_K_PROLOGUE, s);
@@ -140,14 +151,15 @@ cgh_status cgh_ctx::forward_direct(const float *points, const float *A,
     }
     {
         TimedLaunch tl(this, CGH_K_DIRECT_TABLES, s);
-        cudaError_t e = launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp, s);
+        cudaError_t e = launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp,
+                                             count, nsplit, s);
         if (e != cudaSuccess) return cuda_fail(e, "direct tables launch");
         tl.done();
     }
     {
         TimedLaunch tl(this, CGH_K_DIRECT, s);
-        cudaError_t e = launch_direct_forward(tile_index, phx, phy, amp, Npad,
-                                              Nx, Ny, out, d_status, s);
+        cudaError_t e = launch_direct_forward(tile_index, phx, phy, amp, Npad, Nx,
+                                              Ny, out, d, part, count, d_status, s);
         if (e != cudaSuccess) return cuda_fail(e, "direct kernel launch");
         tl.done();
     }
@@ -477,6 +489,15 @@ cgh_status cgh_set_direct_tile(cgh_handle h, const cgh_direct_tile *tile) {
                        "tile %dx%d/%dx%d/%d/%d/%d/%d not compiled in", t.tx, t.ty,
                        t.vx, t.vy, t.pt, t.np, t.g, t.pk);
     h->forced_tile = i;
+    return CGH_OK;
+}
+
+cgh_status cgh_set_direct_schedule(cgh_handle h, int schedule) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    if (schedule != CGH_SCHED_AUTO && schedule != CGH_SCHED_GRID &&
+        schedule != CGH_SCHED_SPLIT)
+        return h->fail(CGH_ERR_INVALID_ARG, "unknown direct schedule %d", schedule);
+    h->direct_schedule = schedule;
     return CGH_OK;
 }
 

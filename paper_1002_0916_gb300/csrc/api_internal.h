@@ -62,6 +62,7 @@ struct cgh_ctx {
     void timer_reset();
 
     int forced_tile = -1;                         // direct tile override
+    int direct_schedule = CGH_SCHED_AUTO;         // cgh_set_direct_schedule
     // fault injection: workspace allocations left before one is made to
     // fail (-1: never); set from CGH_FAIL_ALLOC_AFTER at cgh_create
     int fail_alloc_after = -1;

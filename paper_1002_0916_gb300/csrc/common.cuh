@@ -182,12 +182,26 @@ int direct_tile_count();
 DirectTile direct_tile_get(int i);
 int direct_tile_index(const DirectTile &t);
 size_t direct_phase_table_floats(const DirectTile &t, int Npad, int Nx, int Ny);
+// (zero, nzero): words the tables kernel sets to zero (the split
+// schedule's arrival counters), or (nullptr, 0)
 cudaError_t launch_direct_tables(const PointRec *rec, int Npad, int Nx, int Ny,
                                  const DirectTile &t, float *phx, float *phy,
-                                 float *amp, cudaStream_t s);
+                                 float *amp, unsigned *zero, int nzero,
+                                 cudaStream_t s);
+// Tail split of the direct kernel: `tiles` pixel tiles, those from `tail`
+// on each cut into m chunks of point stages (tail == tiles: none).
+struct DirectSplit {
+    int tiles, tail, m;
+    int chunks() const { return (tiles - tail) * m; }
+};
+DirectSplit direct_split_plan(int tile_index, int sm_count, int Npad, int Nx,
+                              int Ny, bool split);
+// part: chunks() partial tiles; count: tiles - tail words, zero at launch
 cudaError_t launch_direct_forward(int tile_index, const float *phx,
                                   const float *phy, const float *amp, int Npad,
-                                  int Nx, int Ny, float *out, unsigned *status,
+                                  int Nx, int Ny, float *out,
+                                  const DirectSplit &d, float *part,
+                                  unsigned *count, unsigned *status,
                                   cudaStream_t s);
 cudaError_t launch_naive_forward(const PointRec *rec, int N, int Nx, int Ny,
                                  float *out, cudaStream_t s);

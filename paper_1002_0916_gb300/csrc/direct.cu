@@ -41,10 +41,18 @@ __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
                                      int Npad, int TX, int TY, int nxt,
                                      int nyt, float *__restrict__ phx,
                                      float *__restrict__ phy,
-                                     float *__restrict__ amp) {
+                                     float *__restrict__ amp,
+                                     unsigned *__restrict__ zero, int nzero) {
     __shared__ PointRec srec[DT_POINTS];
     pdl_wait();  // the records come from the kernel before
     pdl_trigger();
+    // the split schedule's per-tile arrival counters start at zero (every
+    // earlier kernel on the stream has finished: the prologue before this
+    // launch waits for them)
+    if (blockIdx.x == 0)
+        for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nzero;
+             k += gridDim.y * blockDim.x)
+            zero[k] = 0u;
     const int j0 = blockIdx.x * DT_POINTS;
     if (threadIdx.x < DT_POINTS && j0 + (int)threadIdx.x < Npad)
         srec[threadIdx.x] = rec[j0 + threadIdx.x];
@@ -74,32 +82,86 @@ __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
 }
 
 // ------------------------------------------------------- direct kernel
+// One CTA per pixel tile (1-D grid, tiles in row-major order), except for
+// the last tiles when their count does not spread evenly over the SMs: the
+// tiles from `tail` on are each cut into `m` chunks of point stages, one CTA
+// per chunk, placed after the whole tiles in the grid so that they fill the
+// SMs that finish first.  Each chunk CTA writes its partial tile to `part`
+// (slot = chunk index) and counts itself in count[tile - tail]; the last to
+// arrive adds the m partials in chunk order -- the same order whoever is
+// last, so the result is deterministic -- and writes the tile.  No CTA waits
+// for another.
 template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G, int PK>
 __global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST, G>::THREADS)
 direct_fwd_kernel(const float *__restrict__ phx, const float *__restrict__ phy,
                   const float *__restrict__ amp, int Npad, int Nx, int Ny,
-                  float *__restrict__ out, int vec_store, unsigned *status) {
+                  int nxt, int tail, int m, float *__restrict__ out,
+                  int vec_store, float *__restrict__ part,
+                  unsigned *__restrict__ count, unsigned *status) {
     using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>;
+    using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;
+    __shared__ int s_last;
 
-    const int xt = blockIdx.x, yt = blockIdx.y;
     if (threadIdx.x == 0) {
         abort_flag = 0;
         for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
-    pdl_wait();  // the tables come from the kernel before
+    pdl_wait();  // the tables (and zeroed counters) come from the kernel before
     __syncthreads();
 
+    const int nst = Npad / PT;  // point stages per tile
+    int tile = (int)blockIdx.x, s0 = 0, s1 = nst, q = -1;
+    if (tile >= tail) {  // a chunk of a split tile
+        q = tile - tail;
+        tile = tail + q / m;
+        const int k = q % m;
+        s0 = (int)((long long)nst * k / m);
+        s1 = (int)((long long)nst * (k + 1) / m);
+    }
+    const int xt = tile % nxt, yt = tile / nxt;
     typename L::Acc acc;
     acc.zero();
-    if (!L::accumulate(smem, full, &abort_flag, phx + (size_t)xt * Npad * TX,
-                       phy + (size_t)yt * Npad * TY, amp, Npad / PT, 0u, acc,
-                       status))
+    if (!L::accumulate(smem, full, &abort_flag,
+                       phx + (size_t)xt * Npad * TX + (size_t)s0 * S::SX,
+                       phy + (size_t)yt * Npad * TY + (size_t)s0 * S::SY,
+                       amp + (size_t)s0 * PT, s1 - s0, 0u, acc, status))
         return;
-    L::store(acc, smem, xt, yt, Nx, Ny, out, vec_store);
+    if (q < 0) {
+        L::store(acc, smem, xt, yt, Nx, Ny, out, vec_store);
+        return;
+    }
+    // publish this chunk's partial tile, then count in
+    L::reduce_groups(acc, smem);
+    const int lt = threadIdx.x % S::GT, grp = threadIdx.x / S::GT;
+    const int tx = lt % S::NTX, ty = lt / S::NTX;
+    const int off = (ty * VY) * TX + tx * VX;
+    if (grp == 0) {
+        float *dst = part + (size_t)q * TX * TY + off;
+#pragma unroll
+        for (int r = 0; r < VY; ++r)
+#pragma unroll
+            for (int k = 0; k < VX; ++k) dst[r * TX + k] = acc.get(r, k);
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_last = atomicAdd(&count[tile - tail], 1u) == (unsigned)(m - 1);
+    __syncthreads();
+    if (s_last && grp == 0) {
+        __threadfence();
+        acc.zero();
+        const float *src = part + (size_t)(tile - tail) * m * TX * TY + off;
+        for (int k = 0; k < m; ++k, src += TX * TY)
+#pragma unroll
+            for (int r = 0; r < VY; ++r)
+#pragma unroll
+                for (int c = 0; c < VX; ++c) acc.add(r, c, __ldcg(src + r * TX + c));
+        L::write_out(acc, xt, yt, Nx, Ny, out, vec_store);
+    }
 }
 
 // ------------------------------------------------------- naive kernel
@@ -148,18 +210,41 @@ size_t direct_phase_table_floats(const DirectTile &t, int Npad, int Nx,
 
 cudaError_t launch_direct_tables(const PointRec *rec, int Npad, int Nx, int Ny,
                                  const DirectTile &t, float *phx, float *phy,
-                                 float *amp, cudaStream_t s) {
+                                 float *amp, unsigned *zero, int nzero,
+                                 cudaStream_t s) {
     int nxt = (Nx + t.tx - 1) / t.tx, nyt = (Ny + t.ty - 1) / t.ty;
     const int span = nxt * t.tx + nyt * t.ty;  // <= 65536 + 2 tiles
     dim3 grid((Npad + DT_POINTS - 1) / DT_POINTS, (span + 255) / 256);
     return launch_dependent(direct_tables_kernel, grid, dim3(256), 0, s, rec, Npad,
-                            t.tx, t.ty, nxt, nyt, phx, phy, amp);
+                            t.tx, t.ty, nxt, nyt, phx, phy, amp, zero, nzero);
+}
+
+DirectSplit direct_split_plan(int tile_index, int sm_count, int Npad, int Nx,
+                              int Ny, bool split) {
+    const DirectTile &t = kTiles[tile_index];
+    DirectSplit d;
+    d.tiles = ((Nx + t.tx - 1) / t.tx) * ((Ny + t.ty - 1) / t.ty);
+    d.tail = d.tiles;
+    d.m = 1;
+    const int nst = Npad / t.pt;
+    const int rem = sm_count > 0 ? d.tiles % sm_count : 0;
+    if (!split || rem == 0 || nst < 2) return d;
+    // the last `rem` tiles, each cut into about 2 SMs' worth / rem chunks
+    d.tail = d.tiles - rem;
+    d.m = (2 * sm_count + rem - 1) / rem;
+    if (d.m > nst) d.m = nst;
+    if (d.m < 2) {
+        d.tail = d.tiles;
+        d.m = 1;
+    }
+    return d;
 }
 
 template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G, int PK>
 static cudaError_t launch_one(const float *phx, const float *phy,
                               const float *amp, int Npad, int Nx, int Ny,
-                              float *out, unsigned *status, cudaStream_t s) {
+                              float *out, const DirectSplit &d, float *part,
+                              unsigned *count, unsigned *status, cudaStream_t s) {
     using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
     auto kern = direct_fwd_kernel<TX, TY, VX, VY, PT, NST, NP, G, PK>;
     static bool attr_set[64] = {};
@@ -171,22 +256,26 @@ static cudaError_t launch_one(const float *phx, const float *phy,
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    dim3 grid((Nx + TX - 1) / TX, (Ny + TY - 1) / TY);
+    const int nxt = (Nx + TX - 1) / TX;
+    const unsigned grid = (unsigned)d.tail + (unsigned)(d.tiles - d.tail) * d.m;
     int vec_store = (Nx % 4 == 0) && (((uintptr_t)out & 15) == 0);
-    return launch_dependent(kern, grid, dim3(S::THREADS), S::SMEM, s, phx, phy, amp,
-                            Npad, Nx, Ny, out, vec_store, status);
+    return launch_dependent(kern, dim3(grid), dim3(S::THREADS), S::SMEM, s, phx, phy,
+                            amp, Npad, Nx, Ny, nxt, d.tail, d.m, out, vec_store, part,
+                            count, status);
 }
 
 cudaError_t launch_direct_forward(int tile_index, const float *phx,
                                   const float *phy, const float *amp, int Npad,
-                                  int Nx, int Ny, float *out, unsigned *status,
+                                  int Nx, int Ny, float *out,
+                                  const DirectSplit &d, float *part,
+                                  unsigned *count, unsigned *status,
                                   cudaStream_t s) {
+    if (d.tail < d.tiles && (!part || !count)) return cudaErrorInvalidValue;
     int i = 0;
 #define X(tx, ty, vx, vy, pt, ns, np, g, pk)                                   \
     if (tile_index == i)                                                       \
-        return launch_one<tx, ty, vx, vy, pt, ns, np, g, pk>(phx, phy, amp,    \
-                                                             Npad, Nx, Ny,     \
-                                                             out, status, s);  \
+        return launch_one<tx, ty, vx, vy, pt, ns, np, g, pk>(                   \
+            phx, phy, amp, Npad, Nx, Ny, out, d, part, count, status, s);      \
     ++i;
     CGH_DIRECT_TILES(X)
 #undef X

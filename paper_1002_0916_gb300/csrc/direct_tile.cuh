@@ -331,56 +331,69 @@ struct DirectTileLoop {
         return true;
     }
 
-    // Store the pixels of pixel tile (xt, yt).  With G > 1 the groups other
-    // than the first leave their partial sums in the (now idle) stage ring
-    // and the first group adds them in group order: deterministic.  Ends
-    // with the ring free for the next copies of a persistent CTA.
-    __device__ static void store(Acc &acc, float *smem, int xt, int yt, int Nx,
-                                 int Ny, float *out, int vec_store) {
+    // Add the G groups' partial sums into the first group's accumulators:
+    // the other groups leave theirs in the (now idle) stage ring and the
+    // first group adds them in group order (deterministic).  The ring is in
+    // use until the caller's next __syncthreads.
+    __device__ static void reduce_groups(Acc &acc, float *smem) {
+        if (G == 1) return;
         const int lt = threadIdx.x % S::GT, grp = threadIdx.x / S::GT;
         const int tx = lt % S::NTX, ty = lt / S::NTX;
-        if (G > 1) {
-            if (grp > 0) {
-                float *part = smem + (size_t)(grp - 1) * TX * TY;
+        if (grp > 0) {
+            float *part = smem + (size_t)(grp - 1) * TX * TY;
+#pragma unroll
+            for (int i = 0; i < VY; ++i)
+#pragma unroll
+                for (int k = 0; k < VX; ++k)
+                    part[(ty * VY + i) * TX + tx * VX + k] = acc.get(i, k);
+        }
+        __syncthreads();
+        if (grp == 0) {
+#pragma unroll
+            for (int g = 1; g < G; ++g) {
+                const float *part = smem + (size_t)(g - 1) * TX * TY;
 #pragma unroll
                 for (int i = 0; i < VY; ++i)
 #pragma unroll
                     for (int k = 0; k < VX; ++k)
-                        part[(ty * VY + i) * TX + tx * VX + k] = acc.get(i, k);
-            }
-            __syncthreads();
-            if (grp == 0) {
-#pragma unroll
-                for (int g = 1; g < G; ++g) {
-                    const float *part = smem + (size_t)(g - 1) * TX * TY;
-#pragma unroll
-                    for (int i = 0; i < VY; ++i)
-#pragma unroll
-                        for (int k = 0; k < VX; ++k)
-                            acc.add(i, k, part[(ty * VY + i) * TX + tx * VX + k]);
-                }
+                        acc.add(i, k, part[(ty * VY + i) * TX + tx * VX + k]);
             }
         }
-        if (grp == 0) {
-            const int x0 = xt * TX + tx * VX, y0 = yt * TY + ty * VY;
+    }
+
+    // The first group writes its pixels of pixel tile (xt, yt) to the frame
+    // (clipped to Nx x Ny).
+    __device__ static void write_out(const Acc &acc, int xt, int yt, int Nx,
+                                     int Ny, float *out, int vec_store) {
+        const int lt = threadIdx.x % S::GT, grp = threadIdx.x / S::GT;
+        const int tx = lt % S::NTX, ty = lt / S::NTX;
+        if (grp != 0) return;
+        const int x0 = xt * TX + tx * VX, y0 = yt * TY + ty * VY;
 #pragma unroll
-            for (int i = 0; i < VY; ++i) {
-                const int y = y0 + i;
-                if (y >= Ny) break;
-                float *orow = out + (size_t)y * Nx;
-                if (VX % 4 == 0 && vec_store && x0 + VX <= Nx) {
+        for (int i = 0; i < VY; ++i) {
+            const int y = y0 + i;
+            if (y >= Ny) break;
+            float *orow = out + (size_t)y * Nx;
+            if (VX % 4 == 0 && vec_store && x0 + VX <= Nx) {
 #pragma unroll
-                    for (int k = 0; k < VX; k += 4)
-                        *reinterpret_cast<float4 *>(orow + x0 + k) =
-                            make_float4(acc.get(i, k), acc.get(i, k + 1),
-                                        acc.get(i, k + 2), acc.get(i, k + 3));
-                } else {
+                for (int k = 0; k < VX; k += 4)
+                    *reinterpret_cast<float4 *>(orow + x0 + k) =
+                        make_float4(acc.get(i, k), acc.get(i, k + 1),
+                                    acc.get(i, k + 2), acc.get(i, k + 3));
+            } else {
 #pragma unroll
-                    for (int k = 0; k < VX; ++k)
-                        if (x0 + k < Nx) orow[x0 + k] = acc.get(i, k);
-                }
+                for (int k = 0; k < VX; ++k)
+                    if (x0 + k < Nx) orow[x0 + k] = acc.get(i, k);
             }
         }
+    }
+
+    // Store the pixels of pixel tile (xt, yt).  Ends with the ring free for
+    // the next copies of a persistent CTA.
+    __device__ static void store(Acc &acc, float *smem, int xt, int yt, int Nx,
+                                 int Ny, float *out, int vec_store) {
+        reduce_groups(acc, smem);
+        write_out(acc, xt, yt, Nx, Ny, out, vec_store);
         if (G > 1) __syncthreads();
     }
 };

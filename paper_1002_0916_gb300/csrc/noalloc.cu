@@ -114,10 +114,12 @@ extern "C" cgh_status cgh_forward_noalloc(const float *points, const float *A,
     if (e == cudaSuccess && N > 0) {
         e = launch_prologue(points, A, z, N, Npad, lambda, p, rec, status, s);
         if (e == cudaSuccess)
-            e = launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp, s);
+            e = launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp, nullptr, 0, s);
         if (e == cudaSuccess)
-            e = launch_direct_forward(tile_index, phx, phy, amp, Npad, Nx, Ny,
-                                      out, status, s);
+            e = launch_direct_forward(tile_index, phx, phy, amp, Npad, Nx, Ny, out,
+                                      direct_split_plan(tile_index, 0, Npad, Nx,
+                                                        Ny, false),
+                                      nullptr, nullptr, status, s);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -199,3 +199,44 @@ def test_launch_count_and_autotune(cg, h, oracle_mod):
     assert tile in cg.cgh_direct_tiles()
     err = max_abs(_fwd(cg, h, c), oracle_mod.forward(c))
     assert err <= TOL * sum_abs_A(c)
+
+
+@pytest.mark.parametrize("N,Nx,Ny", [
+    (4096, 32, 32),      # one tile, cut into one chunk per point stage
+    (1000, 100, 70),     # a few tiles, all of them split
+    (257, 1920, 1024),   # 1920 tiles: the last 96 split into uneven chunks
+    (64, 33, 1),         # a single point stage: nothing to split
+])
+def test_split_schedule(cg, h, oracle_mod, N, Nx, Ny):
+    """The tail-split schedule against the oracle and the one-CTA-per-tile
+    grid: every tile shape, deterministic from call to call."""
+    c = make_cloud(300 + N, N, Nx, Ny, integer=False, zlo=0.3, zhi=1.2,
+                   lam=532e-9, p=8e-6)
+    rows = None if Ny <= 128 else sample_rows(Ny, 6, seed=N)
+    ref = oracle_mod.forward(c, rows=rows)
+    tol = TOL * sum_abs_A(c)
+    try:
+        for tile in cg.cgh_direct_tiles()[:: 1 if Nx * Ny < 10**5 else 4]:
+            cg.cgh_set_direct_tile(h, tile)
+            cg.cgh_set_direct_schedule(h, "split")
+            s1 = _fwd(cg, h, c)
+            s2 = _fwd(cg, h, c)
+            assert np.array_equal(s1, s2), tile
+            cg.cgh_set_direct_schedule(h, "grid")
+            g = _fwd(cg, h, c)
+            assert cg.cgh_last_device_status(h) == cg.CGH_OK
+            got = s1 if rows is None else s1[rows]
+            assert max_abs(got, ref) <= tol, tile
+            # same terms, different summation order only
+            assert max_abs(s1, g) <= 1e-5 * sum_abs_A(c), tile
+    finally:
+        cg.cgh_set_direct_schedule(h, "auto")
+        cg.cgh_set_direct_tile(h, None)
+
+
+def test_schedule_argument_errors(cg, h):
+    with pytest.raises(KeyError):
+        cg.cgh_set_direct_schedule(h, "bogus")
+    assert cg.lib.cgh_set_direct_schedule(h, 7) == cg.CGH_ERR_INVALID_ARG
+    assert cg.lib.cgh_set_direct_schedule(None, 0) == cg.CGH_ERR_INVALID_ARG
+    cg.cgh_set_direct_schedule(h, "auto")
