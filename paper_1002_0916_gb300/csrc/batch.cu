@@ -510,12 +510,25 @@ __global__ void sep_batch_prologue_kernel(const SepPrep *__restrict__ prep,
         b.rec[j] = make_point_rec(b.points, b.A, b.z, b.N, j, b.lambda, b.p, status);
 }
 
+// Work items of one problem: (point pair, group of ST_ROWS table rows),
+// pairs fastest so that a warp writes contiguous 256-byte rows.
 __global__ void sep_batch_tables_kernel(const SepPrep *__restrict__ prep) {
     const SepPrep &b = prep[blockIdx.y];
-    const long long total = (long long)(b.Nx + b.Ny) * (b.Kp / 2);
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x)
-        sep_table_entry<2>(b.rec, b.N, b.Nx, b.Kp, e, b.Lhi, b.Llo, b.Rhi, b.Rlo);
+    const int pairs = b.Kp / 4;
+    const int groups = (b.Nx + b.Ny + ST_ROWS - 1) / ST_ROWS;
+    const long long total = (long long)pairs * groups;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(w / pairs);
+        const int j0 = 2 * (int)(w - (long long)g * pairs);
+        const int r0 = g * ST_ROWS;
+        const int r1 = r0 + ST_ROWS < b.Nx + b.Ny ? r0 + ST_ROWS : b.Nx + b.Ny;
+        const bool v0 = j0 < b.N, v1 = j0 + 1 < b.N;
+        const PointRec p0 = v0 ? b.rec[j0] : PointRec{};
+        const PointRec p1 = v1 ? b.rec[j0 + 1] : PointRec{};
+        sep_table_rows<2>(p0, p1, v0, v1, b.Nx, b.Kp, j0, r0, r1, b.Lhi, b.Llo,
+                          b.Rhi, b.Rlo);
+    }
 }
 
 // Split-FP16 batch: one prologue launch, one table launch, one persistent
@@ -616,7 +629,8 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
     int maxNpad = 1, max_blocks = 1;
     for (auto &sp : prep) {
         maxNpad = std::max(maxNpad, sp.Npad);
-        long long n = (long long)(sp.Nx + sp.Ny) * (sp.Kp / 2);
+        // work items of the table kernel: point pairs x groups of rows
+        long long n = (long long)(sp.Kp / 4) * ((sp.Nx + sp.Ny + ST_ROWS - 1) / ST_ROWS);
         max_blocks = (int)std::max<long long>(max_blocks, (n + 255) / 256);
     }
     const int np = (int)prep.size();

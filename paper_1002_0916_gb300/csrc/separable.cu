@@ -33,44 +33,8 @@
 namespace cgh {
 
 // Grid: x over pairs of points (128 pairs per block), y over groups of
-// ST_ROWS consecutive table rows from row0.  Each thread loads its two
-// records once, evaluates the axis phase of its first row directly and then
-// steps it row by row with the exact fixed-point form of Eq. 2 (the phase
-// difference c (2u + 1) - b and its constant second difference 2c, all
-// modulo one turn), and writes the four interleaved entries of the pair as
-// one 8-byte store per plane.
-constexpr int ST_ROWS = 16;
+// ST_ROWS consecutive table rows from row0 (sep_table_rows, sep_table.cuh).
 constexpr int ST_PAIRS = 128;
-
-template <int KIND>
-__device__ __forceinline__ void sep_value(float A, bool valid, bool is_x,
-                                          uint64_t ph, float &re, float &im) {
-    float s, c;
-    __sincosf((float)phase_hi(ph) * RAD_PER_U32, &s, &c);
-    re = valid ? (is_x ? A * c : c) : 0.0f;
-    im = valid ? (is_x ? -A * s : s) : 0.0f;
-}
-
-template <int KIND>
-__device__ __forceinline__ void sep_store(void *hi, void *lo, size_t off, float re0,
-                                          float im0, float re1, float im1) {
-    if (KIND == 0) {
-        __nv_bfloat162 v[2] = {__floats2bfloat162_rn(re0, im0),
-                               __floats2bfloat162_rn(re1, im1)};
-        *reinterpret_cast<uint2 *>((__nv_bfloat16 *)hi + off) =
-            *reinterpret_cast<const uint2 *>(v);
-    } else {
-        __half2 v[2] = {__floats2half2_rn(re0, im0), __floats2half2_rn(re1, im1)};
-        *reinterpret_cast<uint2 *>((__half *)hi + off) = *reinterpret_cast<const uint2 *>(v);
-        if (KIND == 2) {
-            const float2 h0 = __half22float2(v[0]), h1 = __half22float2(v[1]);
-            __half2 w[2] = {__floats2half2_rn((re0 - h0.x) * LO_SCALE, (im0 - h0.y) * LO_SCALE),
-                            __floats2half2_rn((re1 - h1.x) * LO_SCALE, (im1 - h1.y) * LO_SCALE)};
-            *reinterpret_cast<uint2 *>((__half *)lo + off) =
-                *reinterpret_cast<const uint2 *>(w);
-        }
-    }
-}
 
 template <int KIND>
 __global__ void __launch_bounds__(ST_PAIRS)
@@ -86,33 +50,7 @@ sep_tables_kernel(const PointRec *__restrict__ rec, int N, int Nx, int Ny, int K
     const bool v0 = j0 < N, v1 = j0 + 1 < N;
     const PointRec p0 = v0 ? rec[j0] : PointRec{};
     const PointRec p1 = v1 ? rec[j0 + 1] : PointRec{};
-#pragma unroll
-    for (int seg = 0; seg < 2; ++seg) {  // the x rows, then the y rows
-        const bool is_x = seg == 0;
-        const int a = is_x ? r0 : (r0 > Nx ? r0 : Nx);
-        const int b = is_x ? (r1 < Nx ? r1 : Nx) : r1;
-        if (a >= b) continue;
-        int u = is_x ? a : a - Nx;
-        const uint64_t b0 = is_x ? p0.bx : p0.by, b1 = is_x ? p1.bx : p1.by;
-        uint64_t ph0 = axis_phase(p0.c, b0, is_x ? p0.ax : p0.ay, u);
-        uint64_t ph1 = axis_phase(p1.c, b1, is_x ? p1.ax : p1.ay, u);
-        const uint64_t step = (uint64_t)(2 * (int64_t)u + 1);
-        uint64_t d0 = p0.c * step - b0, d1 = p1.c * step - b1;
-        const uint64_t dd0 = 2 * p0.c, dd1 = 2 * p1.c;
-        void *hi = is_x ? Lhi : Rhi;
-        void *lo = is_x ? Llo : Rlo;
-        size_t off = (size_t)u * Kp + 2 * (size_t)j0;
-        for (int r = a; r < b; ++r, off += Kp) {
-            float re0, im0, re1, im1;
-            sep_value<KIND>(p0.A, v0, is_x, ph0, re0, im0);
-            sep_value<KIND>(p1.A, v1, is_x, ph1, re1, im1);
-            sep_store<KIND>(hi, lo, off, re0, im0, re1, im1);
-            ph0 += d0;
-            d0 += dd0;
-            ph1 += d1;
-            d1 += dd1;
-        }
-    }
+    sep_table_rows<KIND>(p0, p1, v0, v1, Nx, Kp, j0, r0, r1, Lhi, Llo, Rhi, Rlo);
 }
 
 cudaError_t launch_sep_tables(const PointRec *rec, int N, int Npad, int Nx,
