@@ -45,6 +45,12 @@ FP32_PER_CLK_PER_SM = 128    # FP32 lanes of the FMA pipe per SM per clock
 # updates per clock per SM.  (Issue slots do not bind: packed FP32x2
 # instructions do two of these operations per slot.)
 MIXED_PP_PER_CLK_PER_SM = 16.0 * 14.0 / 9.0
+# The direct adjoint per update: hardware path = angle add, argument scale,
+# sin + cos (2 MUFU), 6 accumulation ops (8 FP32 ops); polynomial path =
+# add, fold, square, 5 + 5 FMA (cos and sin), times u, 6 accumulation ops
+# (20 FP32 ops, no MUFU).  FMA-pipe limit 128 / (8 + 12 s), MUFU limit
+# 16 / (2 (1 - s)): they meet at s = 2/7, 11.2 updates per clock per SM.
+ADJ_MIXED_PP_PER_CLK_PER_SM = 8.0 * 7.0 / 5.0
 NOMINAL_SMS = 152
 NOMINAL_MAX_MHZ = 2070.0
 FP16_OVER_BF16 = 1.0         # dense FP16 and BF16 tensor rates are equal
@@ -436,8 +442,11 @@ def run_ours(args):
                                default=c.pp)}[dom]
         achieved = pp_dom / (dom_ms / 1e3) / 1e9
         if dom == "bwd_direct":
-            # sin and cos per update: two MUFU operations
-            per_clk, src = MUFU_PER_CLK_PER_SM / 2.0, "16 MUFU ops/clk/SM / 2 per update"
+            per_clk = ADJ_MIXED_PP_PER_CLK_PER_SM
+            src = ("FMA-pipe (128 FP32 ops/clk/SM) and MUFU (16 ops/clk/SM) limits of "
+                   "the adjoint recipe: 8 FP32 ops + 2 MUFU (sin, cos) per hardware "
+                   "update, 20 FP32 ops per polynomial update, best mix 2/7 -> 11.2 "
+                   "updates/clk/SM")
         else:
             per_clk = MIXED_PP_PER_CLK_PER_SM
             src = ("FMA-pipe (128 FP32 ops/clk/SM) and MUFU (16 cosines/clk/SM) limits "
@@ -449,9 +458,9 @@ def run_ours(args):
                 "unit": "Gpp/s", "frac": achieved / peak,
                 "peak_source": f"derived: {sms} SMs x {NOMINAL_MAX_MHZ:.0f} MHz max SM "
                                f"clock x {per_clk:.2f} updates/clk/SM ({src})"}
-        if dom != "bwd_direct":
-            roof["frac_mufu_only"] = achieved / (
-                sms * MUFU_PER_CLK_PER_SM * NOMINAL_MAX_MHZ * 1e6 / 1e9)
+        mufu_per_pp = 2.0 if dom == "bwd_direct" else 1.0
+        roof["frac_mufu_only"] = achieved / (
+            sms * MUFU_PER_CLK_PER_SM / mufu_per_pp * NOMINAL_MAX_MHZ * 1e6 / 1e9)
         if clocks and clocks.get("sm_mhz"):
             roof["frac_at_observed_clock"] = achieved / (
                 sms * per_clk * clocks["sm_mhz"] * 1e6 / 1e9)

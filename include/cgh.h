@@ -207,7 +207,9 @@ typedef struct {
     int packed;            /* 0: scalar FP32; 1: packed FP32x2
                               arithmetic on pixel pairs along x,
                               degree-6 polynomial; 2: packed,
-                              degree-5 polynomial                  */
+                              degree-5 polynomial; 3: as 2 with the
+                              polynomial pixel pairs spread over the
+                              thread's block                        */
 } cgh_direct_tile;
 
 /* How the direct kernel spreads its pixel tiles over the SMs (a scheduling

@@ -63,6 +63,9 @@ struct cgh_ctx {
 
     int forced_tile = -1;                         // direct tile override
     int direct_schedule = CGH_SCHED_AUTO;         // cgh_set_direct_schedule
+    // polynomial (FMA-pipe) sin/cos columns of the direct adjoint's 16-column
+    // strips: 0, 4 (default) or 6; CGH_BWD_POLY at cgh_create
+    int bwd_poly = 4;
     // fault injection: workspace allocations left before one is made to
     // fail (-1: never); set from CGH_FAIL_ALLOC_AFTER at cgh_create
     int fail_alloc_after = -1;

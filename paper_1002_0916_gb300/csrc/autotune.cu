@@ -45,7 +45,8 @@ int default_direct_tile(int N, int Nx, int Ny, int sm_count) {
         // to 1 / (pixels per thread).
         const double share = (double)t.np / (t.vx * t.vy);
         double per_pp = 1.0 - 0.65 * std::min(share, 0.25) + 0.3 * std::max(0.0, share - 0.25);
-        if (t.pk) per_pp *= t.pk == 2 ? 0.91 : 0.93;  // degree-5 polynomial: one FMA less
+        // packed: degree-6 0.93, degree-5 (one FMA less) 0.91, interleaved 0.89
+        if (t.pk) per_pp *= t.pk == 3 ? 0.89 : t.pk == 2 ? 0.91 : 0.93;
         per_pp += 0.5 / (t.vx * t.vy) + 0.25 / (t.pt / t.g);
         const double cost = waves * t.tx * t.ty * per_pp;
         if (cost < best - 1e-9) {

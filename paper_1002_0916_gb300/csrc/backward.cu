@@ -15,8 +15,9 @@
 // Direct (FP32): each thread owns one point and walks a 16-pixel-wide
 // column strip of G top to bottom; G rows are read with uniform (broadcast)
 // loads; the x angles of the strip stay in registers and the y angle follows
-// the exact fixed-point form of the paper's Eq. 2 recurrence.  Two MUFU
-// operations (sin, cos) per point-pixel update.
+// the exact fixed-point form of the paper's Eq. 2 recurrence.  A quarter of
+// the columns take sin and cos from FMA-pipe polynomials, the rest from the
+// hardware sincos (two MUFU operations per point-pixel update).
 //
 // Separable (split FP16 on the tensor cores): with U = e^{i th_x},
 // V = e^{i th_y},
@@ -33,9 +34,11 @@
 
 #include "api_internal.h"
 #include "common.cuh"
+#include "cos_poly.h"
 
 namespace cgh {
 
+constexpr float PI_F = 3.14159265358979323846f;
 constexpr float ADJ_LO_SCALE = 4096.0f;
 
 // ------------------------------------------------------------- G prep
@@ -143,13 +146,24 @@ __global__ void adj_tables_kernel(const PointRec *__restrict__ rec, int N,
 }
 
 // ------------------------------------------------------ direct adjoint
+// Each thread owns one point and a BWD_STRIP-column strip; the arithmetic
+// runs on column pairs in packed FP32x2.  NPOLY columns (pairs spread evenly
+// over the strip) take sin and cos from FMA-pipe polynomials (u = |theta| - pi: cos theta = -C(u^2),
+// sin theta = -sign(theta) u S(u^2); cos_poly.h), the others from the
+// hardware sincos (two MUFU operations): per update 8 FP32 operations and 2
+// MUFU on the hardware path, 20 FP32 operations on the polynomial path.  The
+// polynomial columns accumulate the negated sums and are subtracted at the
+// end.
 constexpr int BWD_STRIP = 16;    // pixels per column strip
 constexpr int BWD_THREADS = 128; // points per CTA
 
+template <int NPOLY>
 __global__ void __launch_bounds__(BWD_THREADS)
 direct_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ points,
                   int N, int Npad, int Nx, int Ny, const float *__restrict__ G,
                   float *__restrict__ part_x, float *__restrict__ part_y) {
+    static_assert(NPOLY % 2 == 0 && NPOLY <= BWD_STRIP, "polynomial column pairs");
+    constexpr int NP2 = BWD_STRIP / 2;
     const int strip = blockIdx.x;
     const int j = blockIdx.y * BWD_THREADS + threadIdx.x;
     const int x0 = strip * BWD_STRIP;
@@ -161,11 +175,13 @@ direct_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ po
         xj = points[2 * j];
         yj = points[2 * j + 1];
     }
-    float tx[BWD_STRIP], dx[BWD_STRIP];
+    float2 tx[NP2], dx[NP2];
 #pragma unroll
-    for (int k = 0; k < BWD_STRIP; ++k) {
-        tx[k] = (float)phase_hi(axis_phase(pr.c, pr.bx, pr.ax, x0 + k)) * RAD_PER_U32;
-        dx[k] = (float)(x0 + k) - xj;
+    for (int k = 0; k < NP2; ++k) {
+        tx[k] = make_float2(
+            (float)phase_hi(axis_phase(pr.c, pr.bx, pr.ax, x0 + 2 * k)) * RAD_PER_U32,
+            (float)phase_hi(axis_phase(pr.c, pr.bx, pr.ax, x0 + 2 * k + 1)) * RAD_PER_U32);
+        dx[k] = make_float2((float)(x0 + 2 * k) - xj, (float)(x0 + 2 * k + 1) - xj);
     }
     // y angle by the fixed-point recurrence: th(y+1) = th(y) + d(y),
     // d(y+1) = d(y) + 2c (exact modulo one turn)
@@ -174,7 +190,10 @@ direct_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ po
     const uint64_t d2 = 2 * pr.c;
     const int ncols = Nx - x0 < BWD_STRIP ? Nx - x0 : BWD_STRIP;
     const bool vec = (ncols == BWD_STRIP) && ((Nx & 3) == 0);
-    float sC = 0.0f, sX = 0.0f, sXX = 0.0f, sY = 0.0f, sYY = 0.0f;
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    // hardware-path sums (+) and polynomial-path sums (negated)
+    float2 sC = z2, sX = z2, sXX = z2, nC = z2, nX = z2, nXX = z2;
+    float sY = 0.0f, sYY = 0.0f;
 #pragma unroll 1
     for (int y = 0; y < Ny; ++y) {
         const float ty = (float)phase_hi(th) * RAD_PER_U32;
@@ -182,41 +201,74 @@ direct_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ po
         dth += d2;
         const float dy = (float)y - yj;
         const float *grow = G + (size_t)y * Nx + x0;
-        float g[BWD_STRIP];
+        float2 g[NP2];
         if (vec) {
 #pragma unroll
-            for (int k = 0; k < BWD_STRIP; k += 4) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(grow + k));
-                g[k] = v.x;
-                g[k + 1] = v.y;
-                g[k + 2] = v.z;
-                g[k + 3] = v.w;
+            for (int k = 0; k < NP2; k += 2) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(grow + 2 * k));
+                g[k] = make_float2(v.x, v.y);
+                g[k + 1] = make_float2(v.z, v.w);
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < BWD_STRIP; ++k) g[k] = k < ncols ? __ldg(grow + k) : 0.0f;
+            for (int k = 0; k < NP2; ++k)
+                g[k] = make_float2(2 * k < ncols ? __ldg(grow + 2 * k) : 0.0f,
+                                   2 * k + 1 < ncols ? __ldg(grow + 2 * k + 1) : 0.0f);
         }
-        float rs = 0.0f;
+        const float2 ty2 = make_float2(ty, ty);
+        float2 rs = z2, nrs = z2;
 #pragma unroll
-        for (int k = 0; k < BWD_STRIP; ++k) {
-            float s, c;
-            __sincosf(tx[k] + ty, &s, &c);
-            sC = fmaf(g[k], c, sC);
-            const float sg = g[k] * s;
-            const float t = sg * dx[k];
-            sX += t;
-            sXX = fmaf(t, dx[k], sXX);
-            rs += sg;
+        for (int k = 0; k < NP2; ++k) {
+            const float2 a = __fadd2_rn(tx[k], ty2);
+            // polynomial pairs spread evenly among the hardware ones
+            if (NPOLY > 0 && k % (BWD_STRIP / NPOLY) == 0 && k / (BWD_STRIP / NPOLY) < NPOLY / 2) {
+                const float2 u = make_float2(fabsf(a.x) - PI_F, fabsf(a.y) - PI_F);
+                const float2 w = __fmul2_rn(u, u);
+                float2 c = make_float2(COS5_C5, COS5_C5);
+                c = __ffma2_rn(c, w, make_float2(COS5_C4, COS5_C4));
+                c = __ffma2_rn(c, w, make_float2(COS5_C3, COS5_C3));
+                c = __ffma2_rn(c, w, make_float2(COS5_C2, COS5_C2));
+                c = __ffma2_rn(c, w, make_float2(COS5_C1, COS5_C1));
+                c = __ffma2_rn(c, w, make_float2(COS5_C0, COS5_C0));  // -cos a
+                float2 sn = make_float2(SIN5_C5, SIN5_C5);
+                sn = __ffma2_rn(sn, w, make_float2(SIN5_C4, SIN5_C4));
+                sn = __ffma2_rn(sn, w, make_float2(SIN5_C3, SIN5_C3));
+                sn = __ffma2_rn(sn, w, make_float2(SIN5_C2, SIN5_C2));
+                sn = __ffma2_rn(sn, w, make_float2(SIN5_C1, SIN5_C1));
+                sn = __ffma2_rn(sn, w, make_float2(SIN5_C0, SIN5_C0));
+                float2 v = __fmul2_rn(sn, u);  // sin u
+                // -sin a = sign(a) sin u: flip the sign bit where a < 0
+                v = make_float2(
+                    __int_as_float(__float_as_int(v.x) ^ (__float_as_int(a.x) & 0x80000000)),
+                    __int_as_float(__float_as_int(v.y) ^ (__float_as_int(a.y) & 0x80000000)));
+                nC = __ffma2_rn(g[k], c, nC);
+                const float2 sg = __fmul2_rn(g[k], v);
+                const float2 t = __fmul2_rn(sg, dx[k]);
+                nX = __fadd2_rn(nX, t);
+                nXX = __ffma2_rn(t, dx[k], nXX);
+                nrs = __fadd2_rn(nrs, sg);
+            } else {
+                float2 sv, cv;
+                __sincosf(a.x, &sv.x, &cv.x);
+                __sincosf(a.y, &sv.y, &cv.y);
+                sC = __ffma2_rn(g[k], cv, sC);
+                const float2 sg = __fmul2_rn(g[k], sv);
+                const float2 t = __fmul2_rn(sg, dx[k]);
+                sX = __fadd2_rn(sX, t);
+                sXX = __ffma2_rn(t, dx[k], sXX);
+                rs = __fadd2_rn(rs, sg);
+            }
         }
-        sY = fmaf(rs, dy, sY);
-        sYY = fmaf(rs * dy, dy, sYY);
+        const float r = (rs.x + rs.y) - (nrs.x + nrs.y);
+        sY = fmaf(r, dy, sY);
+        sYY = fmaf(r * dy, dy, sYY);
     }
     if (valid) {
         float *px = part_x + ((size_t)strip * Npad + j) * 3;
         float *py = part_y + ((size_t)strip * Npad + j) * 3;
-        px[0] = sC;
-        px[1] = sX;
-        px[2] = sXX;
+        px[0] = (sC.x + sC.y) - (nC.x + nC.y);
+        px[1] = (sX.x + sX.y) - (nX.x + nX.y);
+        px[2] = (sXX.x + sXX.y) - (nXX.x + nXX.y);
         py[0] = 0.0f;
         py[1] = sY;
         py[2] = sYY;
@@ -304,8 +356,15 @@ static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
     if (!sep) {
         TimedLaunch tl(h, CGH_K_BWD_DIRECT, s);
         dim3 grid(Tx, Npad / BWD_THREADS);
-        direct_bwd_kernel<<<grid, BWD_THREADS, 0, s>>>(rec, points, N, Npad, Nx, Ny,
-                                                        G, part_x, part_y);
+        if (h->bwd_poly == 0)
+            direct_bwd_kernel<0><<<grid, BWD_THREADS, 0, s>>>(rec, points, N, Npad, Nx,
+                                                               Ny, G, part_x, part_y);
+        else if (h->bwd_poly == 6)
+            direct_bwd_kernel<6><<<grid, BWD_THREADS, 0, s>>>(rec, points, N, Npad, Nx,
+                                                               Ny, G, part_x, part_y);
+        else
+            direct_bwd_kernel<4><<<grid, BWD_THREADS, 0, s>>>(rec, points, N, Npad, Nx,
+                                                               Ny, G, part_x, part_y);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return h->cuda_fail(e, "direct adjoint launch");
         tl.done();

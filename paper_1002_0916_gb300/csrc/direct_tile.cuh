@@ -16,7 +16,8 @@ namespace cgh {
 // each stage's points between them (their partial sums are added in a fixed
 // order at the end), and PK: 0 scalar, 1 packed FP32x2 arithmetic on pixel
 // pairs along x (half the issue slots for the adds and FMAs), 2 packed with
-// the degree-5 polynomial.  Every shape has 256
+// the degree-5 polynomial, 3 as 2 with the polynomial pixel pairs spread over
+// the thread's block instead of leading it.  Every shape has 256
 // threads per CTA.
 #define CGH_DIRECT_TILES(X)                \
     X(64, 64, 4, 4, 32, 3, 4, 1, 0)        \
@@ -37,7 +38,9 @@ namespace cgh {
     X(64, 64, 8, 4, 64, 3, 10, 2, 1)       \
     X(32, 32, 4, 4, 64, 3, 4, 4, 2)        \
     X(32, 32, 4, 4, 64, 3, 6, 4, 2)        \
-    X(32, 32, 4, 4, 32, 3, 4, 4, 2)
+    X(32, 32, 4, 4, 32, 3, 4, 4, 2)        \
+    X(32, 32, 4, 4, 64, 3, 4, 4, 3)        \
+    X(32, 32, 4, 4, 64, 3, 6, 4, 3)
 
 // ------------------------------------------------------------- tables
 // Entries of the per-axis angle tables of one problem: x angles laid out
@@ -219,12 +222,24 @@ template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G,
           int PKV>
 struct DirectTileLoop {
     // PKV: 0 scalar arithmetic, 1 packed FP32x2 with the degree-6 polynomial,
-    // 2 packed with the degree-5 polynomial
+    // 2 packed with the degree-5 polynomial, 3 as 2 with the polynomial pairs
+    // interleaved
     static constexpr bool PK = PKV != 0;
     static_assert(NP >= 0 && NP <= VX * VY, "polynomial pixels per thread");
     static_assert(!PK || NP % 2 == 0, "packed pairs take the polynomial together");
     using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
     using Acc = DirectAcc<VY, VX, PK>;
+
+    // Packed tiles: which pixel pairs take the polynomial -- the first NP / 2
+    // (PKV 1, 2), or NP / 2 pairs spread evenly over the thread's pixels so
+    // that polynomial and MUFU work alternate in the instruction stream (3).
+    static constexpr bool is_poly_pair(int pair) {
+        constexpr int npairs = VX * VY / 2, npoly = NP / 2;
+        if (PKV != 3) return pair < npoly;
+        if (npoly == 0) return false;
+        constexpr int spread = npairs / (npoly > 0 ? npoly : 1);
+        return pair % spread == 0 && pair / spread < npoly;
+    }
 
     __device__ static void issue(float *smem, uint64_t *full, const float *gx,
                                  const float *gy, const float *amp, int t,
@@ -286,8 +301,8 @@ struct DirectTileLoop {
                                 const float2 th =
                                     __fadd2_rn(make_float2(vx[k], vx[k + 1]), y2);
                                 float2 &ac = acc.v[i][k >> 1];
-                                if (i * VX + k < NP)
-                                    ac = __ffma2_rn(na2, neg_cos_poly2<PKV == 2 ? 5 : 6>(th),
+                                if (is_poly_pair((i * VX + k) / 2))
+                                    ac = __ffma2_rn(na2, neg_cos_poly2<PKV == 1 ? 6 : 5>(th),
                                                     ac);
                                 else
                                     ac = __ffma2_rn(

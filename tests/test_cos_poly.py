@@ -42,3 +42,26 @@ def test_polynomial_has_the_taylor_leading_terms():
     assert len(c) == 7
     assert abs(c[0] - 1.0) < 1e-6 and abs(c[1] + 0.5) < 1e-5
     assert abs(c[2] - 1.0 / 24) < 1e-5
+
+
+def _kernel_sin(theta):
+    """The adjoint kernel's sine: u = |theta| - pi, sin theta = -sign(theta)
+    u S(u^2), Horner in float32."""
+    c = _coeffs("SIN5_C")
+    t = theta.astype(np.float32)
+    u = (np.abs(t) - np.float32(np.pi)).astype(np.float32)
+    s = (u * u).astype(np.float32)
+    p = np.full_like(s, c[-1])
+    for k in range(len(c) - 2, -1, -1):
+        p = (p * s + c[k]).astype(np.float32)
+    v = (p * u).astype(np.float32)
+    return np.where(t < 0, v, -v)
+
+
+def test_sine_polynomial_error_bound():
+    th = np.linspace(-2 * np.pi + 1e-6, 2 * np.pi - 1e-6, 400001).astype(np.float32)
+    err = np.abs(_kernel_sin(th).astype(np.float64) - np.sin(th.astype(np.float64)))
+    assert err.max() < 1e-6
+    c = _coeffs("SIN5_C")
+    assert len(c) == 6
+    assert abs(c[0] - 1.0) < 1e-5 and abs(c[1] + 1.0 / 6) < 1e-5
