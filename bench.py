@@ -51,6 +51,21 @@ MIXED_PP_PER_CLK_PER_SM = 16.0 * 14.0 / 9.0
 # (20 FP32 ops, no MUFU).  FMA-pipe limit 128 / (8 + 12 s), MUFU limit
 # 16 / (2 (1 - s)): they meet at s = 2/7, 11.2 updates per clock per SM.
 ADJ_MIXED_PP_PER_CLK_PER_SM = 8.0 * 7.0 / 5.0
+# The Eq. 2 recurrence kernel (the paper's design) per update: 1 MUFU
+# cosine, 7 issue slots (2 integer adds, shift, or, FMA to radians,
+# argument scale, accumulate): the MUFU binds at 16 updates/clk/SM.
+RECUR_PP_PER_CLK_PER_SM = 16.0
+# The FP32 separable product (angle addition) per update: 2 FP32
+# multiply-adds on the FMA pipe, no MUFU: 128 / 2 = 64 updates/clk/SM.
+SIMT_PP_PER_CLK_PER_SM = 64.0
+# The paper's Table 1 (1,920 x 1,024 pixels), times in ms, for context.
+PAPER_TABLE1 = {
+    "N": [512, 1024, 1536, 2048, 2560, 3072, 3584],
+    "cpu_one_core_eq2": [30e3, 59e3, 88e3, 115e3, 146e3, 174e3, 204e3],
+    "nvidia_gtx260_cuda23": [33, 59, 85, 112, 139, 165, 192],
+    "amd_hd5850_opencl_unoptimised": [215, 422, 630, 838, 1045, 1252, 1464],
+    "amd_hd5850_opencl_optimised": [19, 31, 44, 56, 68, 80, 93],
+}
 NOMINAL_SMS = 152
 NOMINAL_MAX_MHZ = 2070.0
 FP16_OVER_BF16 = 1.0         # dense FP16 and BF16 tensor rates are equal
@@ -65,12 +80,15 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="host time budget of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--methods", default="direct,sep_fp16x3")
+    ap.add_argument("--methods", default=None,
+                    help="comma-separated methods (default: direct,sep_fp16x3; "
+                         "table1: direct,recur,sep_fp32,sep_fp16x3)")
     ap.add_argument("--workload", default="paper",
-                    choices=["paper", "large", "batch64", "adjoint"],
+                    choices=["paper", "large", "batch64", "adjoint", "table1"],
                     help="paper: 1920x1024x1024 (the headline line); large: "
                          "3840x2160x16384; batch64: 64 uneven holograms; adjoint: "
-                         "1920x1080x4096 forward + adjoint")
+                         "1920x1080x4096 forward + adjoint; table1: the paper's "
+                         "Table 1 sweep, N = 512..3584 at 1920x1024")
     return ap.parse_args()
 
 
@@ -236,12 +254,17 @@ def _traffic_for(kernel: str):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, rec["source"])
-    if not os.path.exists(src):
+    srcs = rec.get("sources") or [rec.get("source")]
+    shas = rec.get("source_sha256")
+    shas = shas if isinstance(shas, list) else [shas]
+    if len(srcs) != len(shas):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if sha != rec.get("source_sha256"):
-        return None
+    for rel, want in zip(srcs, shas):
+        src = os.path.join(ROOT, rel or "")
+        if not rel or not os.path.exists(src):
+            return None
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != want:
+            return None   # the kernel changed since the counters were taken
     return rec.get("dram_bytes_per_launch")
 
 
@@ -250,9 +273,19 @@ class Leg:
     the point-pixel updates it performs, and the tensor-core flops (if any)
     of its GEMM launches."""
 
-    def __init__(self, name, fn, pp, gemm_flops=0.0, gemm_launches=0):
+    def __init__(self, name, fn, pp, gemm_flops=0.0, gemm_launches=0,
+                 kernel=None, method=None, N=None):
         self.name, self.fn, self.pp = name, fn, pp
         self.gemm_flops, self.gemm_launches = gemm_flops, gemm_launches
+        self.kernel = kernel          # the kernel that does this leg's updates
+        self.method, self.N = method or name, N
+
+
+# kernel (cgh_kernel_id name) that carries a forward method's point-pixel work
+MAIN_KERNEL = {"direct": "direct", "naive": "naive", "recur": "recur",
+               "sep_fp32": "simt", "sep_fp16x3": "gemm", "sep_fp16": "gemm",
+               "sep_bf16": "gemm"}
+GEMM_PASSES = {"sep_fp16x3": 3.0, "sep_fp16": 1.0, "sep_bf16": 1.0}
 
 
 def build_legs(cg, h, which, methods, dev, stream):
@@ -266,16 +299,29 @@ def build_legs(cg, h, which, methods, dev, stream):
                 torch.from_numpy(c.z).to(dev))
 
     legs = []
+
+    def forward_leg(c, m, pts, A, z, name):
+        out = torch.empty((c.Ny, c.Nx), dtype=torch.float32, device=dev)
+        fn = (lambda m=m, out=out: cg.cgh_forward(
+            pts, A, z, c.lam, c.p, c.Nx, c.Ny, out=out, method=m, handle=h,
+            stream=stream))
+        mult = GEMM_PASSES.get(m, 0.0)
+        return Leg(name, fn, c.pp, 4.0 * c.pp * mult, 1 if mult else 0,
+                   kernel=MAIN_KERNEL.get(m), method=m, N=c.N)
+
     if which in ("paper", "large"):
         c = workload(WORKLOAD if which == "paper" else "cfg3_3840x2160_n16384")
         pts, A, z = dev_cloud(c)
         for m in methods:
-            out = torch.empty((c.Ny, c.Nx), dtype=torch.float32, device=dev)
-            fn = (lambda m=m, out=out: cg.cgh_forward(
-                pts, A, z, c.lam, c.p, c.Nx, c.Ny, out=out, method=m, handle=h,
-                stream=stream))
-            mult = {"sep_fp16x3": 3.0, "sep_fp16": 1.0, "sep_bf16": 1.0}.get(m, 0.0)
-            legs.append(Leg(m, fn, c.pp, 4.0 * c.pp * mult, 1 if mult else 0))
+            legs.append(forward_leg(c, m, pts, A, z, m))
+        return c, legs
+    if which == "table1":
+        from workloads import TABLE1_POINTS, table1_cloud
+        for n in TABLE1_POINTS:
+            c = table1_cloud(n)
+            pts, A, z = dev_cloud(c)
+            for m in methods:
+                legs.append(forward_leg(c, m, pts, A, z, f"{m}_n{n}"))
         return c, legs
     if which == "batch64":
         clouds = batch_problems(seed=0)
@@ -291,7 +337,8 @@ def build_legs(cg, h, which, methods, dev, stream):
             if m not in ("direct", "sep_fp16x3"):
                 continue
             fn = (lambda m=m: cg.cgh_batch(probs, method=m, handle=h, stream=stream))
-            legs.append(Leg("batch_" + m, fn, pp))
+            legs.append(Leg("batch_" + m, fn, pp,
+                            kernel="batch" if m == "direct" else "batch_sep"))
         return clouds[0], legs
     if which == "adjoint":
         c = workload("cfg5_1920x1080_n4096")
@@ -308,9 +355,11 @@ def build_legs(cg, h, which, methods, dev, stream):
                 pts, A, z, c.lam, c.p, c.Nx, c.Ny, G, method=m, handle=h,
                 stream=stream))
             mult = 3.0 if m == "sep_fp16x3" else 0.0
-            legs.append(Leg(m + "_fwd", f_fwd, c.pp, 4.0 * c.pp * mult, 1 if mult else 0))
+            legs.append(Leg(m + "_fwd", f_fwd, c.pp, 4.0 * c.pp * mult, 1 if mult else 0,
+                            kernel=MAIN_KERNEL[m]))
             legs.append(Leg(m + "_bwd", f_bwd, c.pp, 2 * 4.0 * c.pp * mult,
-                            2 if mult else 0))
+                            2 if mult else 0,
+                            kernel="bwd_direct" if m == "direct" else "bwd_gemm"))
         return c, legs
     raise SystemExit(f"unknown workload {which}")
 
@@ -339,6 +388,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     h = cg.cgh_create(local)
     stream = torch.cuda.current_stream()
+    if args.methods is None:
+        args.methods = ("direct,recur,sep_fp32,sep_fp16x3" if args.workload == "table1"
+                        else "direct,sep_fp16x3")
     methods = [m.strip() for m in args.methods.split(",") if m.strip()]
     c, all_legs = build_legs(cg, h, args.workload, methods, dev, stream)
     legs = []
@@ -436,12 +488,21 @@ def run_ours(args):
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
     sms = props.multi_processor_count
-    if dom in ("direct", "naive", "batch", "bwd_direct"):
-        pp_dom = {"direct": c.pp, "naive": c.pp, "bwd_direct": c.pp,
-                  "batch": max((leg.pp for leg in legs if leg.name == "batch_direct"),
-                               default=c.pp)}[dom]
+    if dom in ("direct", "naive", "batch", "bwd_direct", "recur", "simt"):
+        # point-pixel updates per launch of the dominant kernel: the mean over
+        # the legs it serves (each leg launches it once per step)
+        dom_legs = [leg.pp for leg in legs if leg.kernel == dom]
+        pp_dom = statistics.mean(dom_legs) if dom_legs else c.pp
         achieved = pp_dom / (dom_ms / 1e3) / 1e9
-        if dom == "bwd_direct":
+        if dom == "simt":
+            per_clk = SIMT_PP_PER_CLK_PER_SM
+            src = ("FMA-pipe limit of the FP32 angle-addition product: 2 FP32 "
+                   "multiply-adds per update, 128 per clk/SM")
+        elif dom == "recur":
+            per_clk = RECUR_PP_PER_CLK_PER_SM
+            src = ("MUFU limit of the Eq. 2 recurrence recipe: 1 hardware cosine per "
+                   "update at 16/clk/SM (7 issue slots per update allow 18.3)")
+        elif dom == "bwd_direct":
             per_clk = ADJ_MIXED_PP_PER_CLK_PER_SM
             src = ("FMA-pipe (128 FP32 ops/clk/SM) and MUFU (16 ops/clk/SM) limits of "
                    "the adjoint recipe: 8 FP32 ops + 2 MUFU (sin, cos) per hardware "
@@ -458,9 +519,10 @@ def run_ours(args):
                 "unit": "Gpp/s", "frac": achieved / peak,
                 "peak_source": f"derived: {sms} SMs x {NOMINAL_MAX_MHZ:.0f} MHz max SM "
                                f"clock x {per_clk:.2f} updates/clk/SM ({src})"}
-        mufu_per_pp = 2.0 if dom == "bwd_direct" else 1.0
-        roof["frac_mufu_only"] = achieved / (
-            sms * MUFU_PER_CLK_PER_SM / mufu_per_pp * NOMINAL_MAX_MHZ * 1e6 / 1e9)
+        if dom != "simt":
+            mufu_per_pp = 2.0 if dom == "bwd_direct" else 1.0
+            roof["frac_mufu_only"] = achieved / (
+                sms * MUFU_PER_CLK_PER_SM / mufu_per_pp * NOMINAL_MAX_MHZ * 1e6 / 1e9)
         if clocks and clocks.get("sm_mhz"):
             roof["frac_at_observed_clock"] = achieved / (
                 sms * per_clk * clocks["sm_mhz"] * 1e6 / 1e9)
@@ -510,6 +572,19 @@ def run_ours(args):
                "d2h_bytes_per_step": len(fwd_methods) * c.Nx * c.Ny * 4,
                "ms_per_step": e2e_s * 1e3}
 
+    table1 = None
+    if args.workload == "table1":
+        from workloads import TABLE1_POINTS
+        table1 = {"N": list(TABLE1_POINTS), "ms": {}, "pp_per_s": {},
+                  "paper_table1_ms": PAPER_TABLE1,
+                  "paper_source": "Table 1 of the paper (other machines; context)"}
+        for m in methods:
+            ms_m = [leg_ms[f"{m}_n{n}"] for n in TABLE1_POINTS if f"{m}_n{n}" in leg_ms]
+            if len(ms_m) == len(TABLE1_POINTS):
+                table1["ms"][m] = ms_m
+                table1["pp_per_s"][m] = [n * 1920 * 1024 / (t / 1e3)
+                                         for n, t in zip(TABLE1_POINTS, ms_m)]
+
     line = None
     if rank == 0:
         cfg = {"workload": workload_desc() if args.workload == "paper" else args.workload,
@@ -517,13 +592,19 @@ def run_ours(args):
                "l2": "flushed: 256 MiB device write between timed steps",
                "parallelism": ("replicas (each rank its own copy of the workload)"
                                if world > 1 else "single GPU")}
-        if args.workload != "batch64":
+        if args.workload == "table1":
+            cfg["workload"] = ("1920x1024 pixels, N = 512, 1024, ..., 3584 points (the "
+                               "paper's Table 1 sweep), otherwise the 1920x1024x1024 "
+                               "recipe; one step = every N by every method")
+            cfg.update({"Nx": c.Nx, "Ny": c.Ny, "N": "512..3584 step 512"})
+        elif args.workload != "batch64":
             cfg.update({"Nx": c.Nx, "Ny": c.Ny, "N": c.N})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f16x3" if any("sep" in leg.name for leg in legs) else "f32",
+            "dtype": ("f32+f16x3" if any(leg.method in GEMM_PASSES for leg in legs)
+                      else "f32"),
             "data": "synthetic", "config": cfg,
             "methods": {leg.name: {"ms": leg_ms[leg.name],
                                    "pp_per_s": leg.pp / (leg_ms[leg.name] / 1e3)}
@@ -531,6 +612,8 @@ def run_ours(args):
             "kernels_ms_per_launch": {k: kt[k][0] / kt[k][1] for k in kt if kt[k][1] > 0},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
+        if table1 is not None:
+            line["table1"] = table1
     cg.cgh_destroy(h)
     if dist is not None:
         dist.barrier()

@@ -80,7 +80,21 @@ typedef enum {
     /* One thread per pixel, plain loop over points, 64-bit fixed-point phase
      * and cospif (the unoptimised kernel of the paper's Fig. 2b, restated).
      * Slow; for checking. */
-    CGH_NAIVE_FP32 = 4
+    CGH_NAIVE_FP32 = 4,
+    /* The paper's optimised kernel design (Section 2.1) restated: groups of
+     * 16 x 16 threads, eight consecutive pixels per thread along x, 256
+     * points per shared-memory stage, point loop unrolled by four, the phase
+     * advanced from pixel to pixel by the two recurrences of Eq. 2 (here in
+     * 32-bit fixed-point turns), hardware cosine.  A comparison point for
+     * CGH_DIRECT_FP32 (same accuracy bound). */
+    CGH_RECUR_FP32 = 5,
+    /* The separable form in FP32 on the FMA pipe: with per-axis tables of
+     * A_j (cos, -sin) theta_x and (cos, sin) theta_y (exact fixed-point
+     * phase, accurate sincospi), cos(theta_x + theta_y) is two FP32
+     * multiply-adds per point-pixel update, no special-function operation;
+     * an FP32 matrix product of depth 2N on the SIMT cores.  Same accuracy
+     * bound as CGH_DIRECT_FP32. */
+    CGH_SEP_FP32 = 6
 } cgh_method;
 
 /* Create a handle bound to CUDA device `device` (made current on the calling
@@ -268,6 +282,8 @@ typedef enum {
     CGH_K_BATCH = 9,          /* direct batch (its whole graph)         */
     CGH_K_AUX = 10,           /* small helpers (conversions, fills)     */
     CGH_K_BATCH_SEP = 11,     /* separable batch (its whole graph)      */
+    CGH_K_RECUR = 12,         /* Eq. 2 recurrence kernel                */
+    CGH_K_SIMT = 13,          /* FP32 separable product (FMA pipe)      */
     CGH_K_COUNT = 16
 } cgh_kernel_id;
 

@@ -21,7 +21,9 @@ from typing import Optional, Sequence
 __all__ = [
     "CGH_OK", "CGH_ERR_INVALID_ARG", "CGH_ERR_CUDA", "CGH_ERR_NOMEM",
     "CGH_ERR_UNSUPPORTED", "CGH_ERR_TIMEOUT", "CGH_DIRECT_FP32", "CGH_SEP_BF16",
-    "CGH_SEP_FP16", "CGH_SEP_FP16X3", "CGH_NAIVE_FP32", "METHODS", "CGHError",
+    "CGH_SEP_FP16", "CGH_SEP_FP16X3", "CGH_NAIVE_FP32", "CGH_RECUR_FP32",
+    "CGH_SEP_FP32", "METHODS",
+    "CGHError",
     "lib", "library_path", "cgh_create", "cgh_destroy", "cgh_forward",
     "cgh_forward_host", "cgh_backward", "cgh_batch", "cgh_tune",
     "cgh_set_direct_tile", "cgh_direct_tiles", "cgh_last_device_status",
@@ -34,10 +36,11 @@ __all__ = [
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
 CGH_ERR_NOMEM, CGH_ERR_UNSUPPORTED, CGH_ERR_TIMEOUT = 3, 4, 5
 CGH_DIRECT_FP32, CGH_SEP_BF16, CGH_SEP_FP16 = 0, 1, 2
-CGH_SEP_FP16X3, CGH_NAIVE_FP32 = 3, 4
+CGH_SEP_FP16X3, CGH_NAIVE_FP32, CGH_RECUR_FP32, CGH_SEP_FP32 = 3, 4, 5, 6
 METHODS = {"direct": CGH_DIRECT_FP32, "sep_bf16": CGH_SEP_BF16,
            "sep_fp16": CGH_SEP_FP16, "sep_fp16x3": CGH_SEP_FP16X3,
-           "naive": CGH_NAIVE_FP32}
+           "naive": CGH_NAIVE_FP32, "recur": CGH_RECUR_FP32,
+           "sep_fp32": CGH_SEP_FP32}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "_lib", "libcgh.so")
@@ -365,7 +368,8 @@ def cgh_launch_count(h) -> int:
 
 KERNELS = {"prologue": 0, "direct_tables": 1, "direct": 2, "naive": 3,
            "sep_tables": 4, "gemm": 5, "bwd_direct": 6, "bwd_gemm": 7,
-           "bwd_reduce": 8, "batch": 9, "aux": 10, "batch_sep": 11}
+           "bwd_reduce": 8, "batch": 9, "aux": 10, "batch_sep": 11, "recur": 12,
+           "simt": 13}
 
 
 def cgh_kernel_timing(h, enable: bool = True) -> None:

@@ -190,6 +190,31 @@ cgh_status cgh_ctx::forward_naive(const float *points, const float *A,
     return CGH_OK;
 }
 
+cgh_status cgh_ctx::forward_recur(const float *points, const float *A,
+                                  const float *z, int N, double lambda,
+                                  double p, int Nx, int Ny, float *out,
+                                  cudaStream_t s) {
+    const int Npad = pad_to(N, recur_points_per_stage());
+    const size_t rec_b = align256((size_t)Npad * sizeof(PointRec));
+    cgh_status st = ensure(ws, rec_b, s, "recurrence workspace");
+    if (st) return st;
+    PointRec *rec = (PointRec *)ws.ptr;
+    {
+        TimedLaunch tl(this, CGH_K_PROLOGUE, s);
+        cudaError_t e = launch_prologue(points, A, z, N, Npad, lambda, p, rec,
+                                        d_status, s);
+        if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
+        tl.done();
+    }
+    {
+        TimedLaunch tl(this, CGH_K_RECUR, s);
+        cudaError_t e = launch_recur_forward(rec, Npad, Nx, Ny, out, s);
+        if (e != cudaSuccess) return cuda_fail(e, "recurrence kernel launch");
+        tl.done();
+    }
+    return CGH_OK;
+}
+
 cgh_status cgh_ctx::forward(const float *points, const float *A,
                             const float *z, int N, double lambda, double p,
                             int Nx, int Ny, float *out, int method,
@@ -206,6 +231,10 @@ cgh_status cgh_ctx::forward(const float *points, const float *A,
                               pick_direct_tile(N, Nx, Ny), s);
     case CGH_NAIVE_FP32:
         return forward_naive(points, A, z, N, lambda, p, Nx, Ny, out, s);
+    case CGH_RECUR_FP32:
+        return forward_recur(points, A, z, N, lambda, p, Nx, Ny, out, s);
+    case CGH_SEP_FP32:
+        return forward_simt(points, A, z, N, lambda, p, Nx, Ny, out, s);
     case CGH_SEP_BF16:
     case CGH_SEP_FP16:
     case CGH_SEP_FP16X3:

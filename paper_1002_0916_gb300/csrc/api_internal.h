@@ -89,6 +89,12 @@ struct cgh_ctx {
     cgh_status forward_naive(const float *points, const float *A,
                              const float *z, int N, double lambda, double p,
                              int Nx, int Ny, float *out, cudaStream_t s);
+    cgh_status forward_recur(const float *points, const float *A,
+                             const float *z, int N, double lambda, double p,
+                             int Nx, int Ny, float *out, cudaStream_t s);
+    cgh_status forward_simt(const float *points, const float *A,
+                            const float *z, int N, double lambda, double p,
+                            int Nx, int Ny, float *out, cudaStream_t s);
     cgh_status forward_separable(const float *points, const float *A,
                                  const float *z, int N, double lambda, double p,
                                  int Nx, int Ny, float *out, int method,

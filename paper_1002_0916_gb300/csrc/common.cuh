@@ -206,6 +206,12 @@ cudaError_t launch_direct_forward(int tile_index, const float *phx,
 cudaError_t launch_naive_forward(const PointRec *rec, int N, int Nx, int Ny,
                                  float *out, cudaStream_t s);
 
+// recur.cu: the Eq. 2 recurrence kernel; Npad a multiple of
+// recur_points_per_stage() (records padded with zero amplitude)
+int recur_points_per_stage();
+cudaError_t launch_recur_forward(const PointRec *rec, int Npad, int Nx, int Ny,
+                                 float *out, cudaStream_t s);
+
 // umma.cu: D = A B^T (single pass) or Ahi Bhi^T + lo_scale (Ahi Blo^T +
 // Alo Bhi^T) (split) on the tensor cores.  A: M x K, B: N x K, 16-bit,
 // K-major with row strides lda, ldb (elements); D: FP32, row stride ldd.

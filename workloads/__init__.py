@@ -26,7 +26,7 @@ from typing import List, Optional
 import numpy as np
 
 __all__ = ["Cloud", "make_cloud", "WORKLOADS", "workload", "batch_problems",
-           "grad_field"]
+           "grad_field", "TABLE1_POINTS", "table1_cloud"]
 
 
 @dataclass
@@ -93,6 +93,19 @@ def workload(name: str, seed: int = 0) -> Cloud:
     """The named single-hologram workload drawn with ``seed`` (default 0)."""
     kw = dict(WORKLOADS[name])
     return make_cloud(seed, name=name, **kw)
+
+
+# The point counts of the paper's Table 1 (1,920 x 1,024 pixels).
+TABLE1_POINTS = (512, 1024, 1536, 2048, 2560, 3072, 3584)
+
+
+def table1_cloud(N: int, seed: int = 0) -> Cloud:
+    """A cloud of N points on the paper's Table 1 frame, with the 1920x1024
+    workload's recipe (integer coordinates, z ~ U[0.5, 1.5] m, 633 nm,
+    6.4 um) and only N changed."""
+    kw = dict(WORKLOADS["cfg2_1920x1024_n1024"])
+    kw["N"] = int(N)
+    return make_cloud(seed, name=f"table1_n{N}", **kw)
 
 
 BATCH_WAVELENGTHS = (633e-9, 532e-9, 473e-9)
