@@ -359,6 +359,7 @@ cgh_status cgh_create(cgh_handle *out, int device) {
     }
     h->load_tune_cache();
     if (const char *f = getenv("CGH_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(f);
+    if (const char *f = getenv("CGH_SIMT_STAGE")) h->simt_stage = atoi(f);
     if (const char *f = getenv("CGH_BWD_POLY")) {
         const int v = atoi(f);
         if (v == 0 || v == 4 || v == 6) h->bwd_poly = v;

@@ -66,6 +66,10 @@ struct cgh_ctx {
     // polynomial (FMA-pipe) sin/cos columns of the direct adjoint's 16-column
     // strips: 0, 4 (default) or 6; CGH_BWD_POLY at cgh_create
     int bwd_poly = 4;
+    // stage shape of the FP32 separable product (index into the compiled
+    // shapes; 1 = 32 values of k x 2 stages, the fastest measured);
+    // CGH_SIMT_STAGE at cgh_create
+    int simt_stage = 1;
     // fault injection: workspace allocations left before one is made to
     // fail (-1: never); set from CGH_FAIL_ALLOC_AFTER at cgh_create
     int fail_alloc_after = -1;

@@ -18,7 +18,7 @@
 //    as packed FP32x2 pairs along x (fma.rn.f32x2: two multiply-adds per
 //    issue slot);
 //  * operands staged in shared memory by 1-D bulk copies (cp.async.bulk with
-//    mbarrier completion), SS_NST stages of SS_BK values of k: the tables are
+//    mbarrier completion), NST stages of BK values of k: the tables are
 //    laid out tile by tile ([tile][k][pixel in tile]) so that one stage of
 //    one operand is one contiguous block;
 //  * R entries are stored twice in a row (each value next to itself, in the
@@ -37,15 +37,25 @@ namespace cgh {
 
 constexpr int SS_BM = 128;          // y rows per CTA tile
 constexpr int SS_BN = 128;          // x columns per CTA tile
-constexpr int SS_BK = 16;           // values of k per stage (8 points)
-constexpr int SS_NST = 4;           // stages in flight
 constexpr int SS_THREADS = 256;
-constexpr int SS_LSTAGE = SS_BK * SS_BN;        // floats of L per stage
-constexpr int SS_RSTAGE = SS_BK * 2 * SS_BM;    // floats of R per stage (doubled)
-constexpr int SS_STAGE = SS_LSTAGE + SS_RSTAGE;
-constexpr size_t SS_SMEM = (size_t)SS_NST * SS_STAGE * sizeof(float);
 constexpr int SS_MAX_SPLIT = 16;
-static_assert((SS_LSTAGE * 4) % 16 == 0 && (SS_RSTAGE * 4) % 16 == 0, "bulk sizes");
+constexpr int SS_KPAD = 32;         // K (= 2 Npad) is padded to this multiple
+
+// Stage geometry: BK values of k per stage, NST stages in flight.
+template <int BK, int NST>
+struct SimtStage {
+    static constexpr int L = BK * SS_BN;          // floats of L per stage
+    static constexpr int R = BK * 2 * SS_BM;      // floats of R per stage (doubled)
+    static constexpr int ALL = L + R;
+    static constexpr size_t SMEM = (size_t)NST * ALL * sizeof(float);
+    static_assert((L * 4) % 16 == 0 && (R * 4) % 16 == 0, "bulk sizes");
+    static_assert(SS_KPAD % BK == 0, "K padding covers the stage");
+};
+// The shapes compiled in: (BK, NST).  Measured on the 1920x1024x1024 and
+// 3840x2160x16384 frames, (32, 2) was fastest (fewest barriers per
+// multiply-add at two CTAs per SM); (16, 4) within 3%, (8, 8) and (32, 3)
+// (one CTA per SM) 6-12% slower.
+#define CGH_SIMT_STAGES(X) X(16, 4) X(32, 2) X(8, 8) X(32, 3)
 
 // Position of R value (row i of the tile, copy d) in a doubled R row of
 // 2 * SS_BM floats.  Row i = wy 64 + h 32 + ty 4 + q (warp row wy, half h,
@@ -114,18 +124,20 @@ __global__ void simt_tables_kernel(const PointRec *__restrict__ rec, int Npad,
 }
 
 // ------------------------------------------------------------------ GEMM
+template <int BK, int NST>
 __device__ __forceinline__ void ss_issue(float *smem, uint64_t *full,
                                          const float *Lb, const float *Rb,
                                          int stage, int slot) {
-    float *st = smem + (size_t)slot * SS_STAGE;
-    mbar_arrive_expect_tx(&full[slot], SS_STAGE * 4);
-    bulk_g2s(st, Lb + (size_t)stage * SS_LSTAGE, SS_LSTAGE * 4, &full[slot]);
-    bulk_g2s(st + SS_LSTAGE, Rb + (size_t)stage * SS_RSTAGE, SS_RSTAGE * 4,
-             &full[slot]);
+    using G = SimtStage<BK, NST>;
+    float *st = smem + (size_t)slot * G::ALL;
+    mbar_arrive_expect_tx(&full[slot], G::ALL * 4);
+    bulk_g2s(st, Lb + (size_t)stage * G::L, G::L * 4, &full[slot]);
+    bulk_g2s(st + G::L, Rb + (size_t)stage * G::R, G::R * 4, &full[slot]);
 }
 
 // One unit = (tile, k slice).  Units are numbered tile-major: unit =
 // tile * S + slice.  Tiles are row-major over (x tile, y tile).
+template <int BK, int NST>
 __global__ void __launch_bounds__(SS_THREADS, 2)
 simt_gemm_kernel(const float *__restrict__ Lt, const float *__restrict__ Rt,
                  int Npad, int Nx, int Ny, int nxt, int S,
@@ -133,31 +145,32 @@ simt_gemm_kernel(const float *__restrict__ Lt, const float *__restrict__ Rt,
                  float *__restrict__ part, unsigned *__restrict__ count,
                  unsigned *status) {
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t full[SS_NST];
+    using G = SimtStage<BK, NST>;
+    __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;
     __shared__ int s_last;
 
     const int unit = blockIdx.x;
     const int tile = unit / S, slice = unit - tile * S;
     const int xt = tile % nxt, yt = tile / nxt;
-    const int nst = 2 * Npad / SS_BK;
+    const int nst = 2 * Npad / BK;
     const int s0 = (int)((long long)nst * slice / S);
     const int s1 = (int)((long long)nst * (slice + 1) / S);
     const int ntile = s1 - s0;
     const size_t K = 2 * (size_t)Npad;
-    const float *Lb = Lt + ((size_t)xt * K + (size_t)s0 * SS_BK) * SS_BN;
-    const float *Rb = Rt + ((size_t)yt * K + (size_t)s0 * SS_BK) * (2 * SS_BM);
+    const float *Lb = Lt + ((size_t)xt * K + (size_t)s0 * BK) * SS_BN;
+    const float *Rb = Rt + ((size_t)yt * K + (size_t)s0 * BK) * (2 * SS_BM);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < SS_NST; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
         mbar_fence_init();
     }
     __syncthreads();
     int issued = 0;  // thread 0 only
     if (threadIdx.x == 0)
-        for (int s = 0; s < SS_NST && s < ntile; ++s) {
-            ss_issue(smem, full, Lb, Rb, s, s);
+        for (int s = 0; s < NST && s < ntile; ++s) {
+            ss_issue<BK, NST>(smem, full, Lb, Rb, s, s);
             ++issued;
         }
 
@@ -182,16 +195,16 @@ simt_gemm_kernel(const float *__restrict__ Lt, const float *__restrict__ Rt,
 
     int t = 0;
     for (; t < ntile; ++t) {
-        const int s = t % SS_NST;
-        const uint32_t par = (uint32_t)((t / SS_NST) & 1);
+        const int s = t % NST;
+        const uint32_t par = (uint32_t)((t / NST) & 1);
         if (!mbar_wait_bounded(&full[s], par)) {
             abort_flag = 1;
             set_status(status, DEV_TIMEOUT);
         } else {
-            const float *Ls = smem + (size_t)s * SS_STAGE;
-            const float *Rs = Ls + SS_LSTAGE;
+            const float *Ls = smem + (size_t)s * G::ALL;
+            const float *Rs = Ls + G::L;
 #pragma unroll 2
-            for (int k = 0; k < SS_BK; ++k) {
+            for (int k = 0; k < BK; ++k) {
                 const float4 la = *reinterpret_cast<const float4 *>(Ls + k * SS_BN + cx);
                 const float4 lb =
                     *reinterpret_cast<const float4 *>(Ls + k * SS_BN + cx + 16);
@@ -214,9 +227,9 @@ simt_gemm_kernel(const float *__restrict__ Lt, const float *__restrict__ Rt,
         }
         __syncthreads();  // every thread is done with slot s
         if (abort_flag) break;
-        if (threadIdx.x == 0 && t + SS_NST < ntile) {
+        if (threadIdx.x == 0 && t + NST < ntile) {
             fence_proxy_async_smem();
-            ss_issue(smem, full, Lb, Rb, t + SS_NST, s);
+            ss_issue<BK, NST>(smem, full, Lb, Rb, t + NST, s);
             ++issued;
         }
     }
@@ -224,7 +237,7 @@ simt_gemm_kernel(const float *__restrict__ Lt, const float *__restrict__ Rt,
         // let this CTA's copies still in flight land (each wait bounded)
         if (threadIdx.x == 0)
             for (int u = t; u < issued; ++u)
-                mbar_wait_bounded(&full[u % SS_NST], (uint32_t)((u / SS_NST) & 1));
+                mbar_wait_bounded(&full[u % NST], (uint32_t)((u / NST) & 1));
         return;
     }
 
@@ -290,11 +303,11 @@ simt_gemm_kernel(const float *__restrict__ Lt, const float *__restrict__ Rt,
 }
 
 // Number of k slices for `tiles` output tiles of `nst` stages each: the
-// fewest slices whose units fill the SMs' CTA slots (two per SM) in nearly
-// whole waves, counting about four stages of work per unit for its
+// fewest slices whose units fill the SMs' CTA slots (`per_sm` per SM) in
+// nearly whole waves, counting about four stages of work per unit for its
 // epilogue.
-static int simt_split(int tiles, int nst, int sm_count) {
-    const int slots = 2 * (sm_count > 0 ? sm_count : 1);
+static int simt_split(int tiles, int nst, int sm_count, int per_sm) {
+    const int slots = per_sm * (sm_count > 0 ? sm_count : 1);
     int best = 1;
     double best_cost = 1e300;
     for (int S = 1; S <= SS_MAX_SPLIT && S <= nst; ++S) {
@@ -310,6 +323,68 @@ static int simt_split(int tiles, int nst, int sm_count) {
     return best;
 }
 
+struct SimtPlan {
+    int bk, nst_ring, per_sm;
+};
+
+static SimtPlan simt_plan(int index) {
+    int i = 0;
+#define X(bk, ns)                                                               \
+    if (index == i)                                                             \
+        return SimtPlan{bk, ns,                                                 \
+                        SimtStage<bk, ns>::SMEM <= 110 * 1024 ? 2 : 1};         \
+    ++i;
+    CGH_SIMT_STAGES(X)
+#undef X
+    return SimtPlan{16, 4, 2};
+}
+
+int simt_stage_count() {
+    int n = 0;
+#define X(bk, ns) ++n;
+    CGH_SIMT_STAGES(X)
+#undef X
+    return n;
+}
+
+template <int BK, int NST>
+static cudaError_t launch_simt_gemm(int device, unsigned grid, cudaStream_t s,
+                                    const float *Lt, const float *Rt, int Npad,
+                                    int Nx, int Ny, int nxt, int S, float *out,
+                                    int vec_store, float *part, unsigned *count,
+                                    unsigned *status) {
+    using G = SimtStage<BK, NST>;
+    static bool attr_set[64] = {};
+    if (device < 0 || device >= 64 || !attr_set[device]) {
+        cudaError_t e = cudaFuncSetAttribute(simt_gemm_kernel<BK, NST>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)G::SMEM);
+        if (e != cudaSuccess) return e;
+        if (device >= 0 && device < 64) attr_set[device] = true;
+    }
+    simt_gemm_kernel<BK, NST><<<grid, SS_THREADS, G::SMEM, s>>>(
+        Lt, Rt, Npad, Nx, Ny, nxt, S, out, vec_store, part, count, status);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_simt_index(int index, int device, unsigned grid,
+                                     cudaStream_t s, const float *Lt,
+                                     const float *Rt, int Npad, int Nx, int Ny,
+                                     int nxt, int S, float *out, int vec_store,
+                                     float *part, unsigned *count,
+                                     unsigned *status) {
+    int i = 0;
+#define X(bk, ns)                                                               \
+    if (index == i)                                                             \
+        return launch_simt_gemm<bk, ns>(device, grid, s, Lt, Rt, Npad, Nx, Ny,  \
+                                        nxt, S, out, vec_store, part, count,    \
+                                        status);                                \
+    ++i;
+    CGH_SIMT_STAGES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace cgh
 
 using namespace cgh;
@@ -318,11 +393,13 @@ cgh_status cgh_ctx::forward_simt(const float *points, const float *A,
                                  const float *z, int N, double lambda,
                                  double p, int Nx, int Ny, float *out,
                                  cudaStream_t s) {
-    const int Npad = pad_to(N, SS_BK / 2);
+    const int index = simt_stage >= 0 && simt_stage < simt_stage_count() ? simt_stage : 1;
+    const SimtPlan plan = simt_plan(index);
+    const int Npad = pad_to(N, SS_KPAD / 2);
     const int nxt = (Nx + SS_BN - 1) / SS_BN, nyt = (Ny + SS_BM - 1) / SS_BM;
     const int tiles = nxt * nyt;
-    const int nst = 2 * Npad / SS_BK;
-    const int S = simt_split(tiles, nst, sm_count);
+    const int nst = 2 * Npad / plan.bk;
+    const int S = simt_split(tiles, nst, sm_count, plan.per_sm);
     const size_t K = 2 * (size_t)Npad;
     const size_t rec_b = align256((size_t)Npad * sizeof(PointRec));
     const size_t l_b = align256((size_t)nxt * K * SS_BN * sizeof(float));
@@ -357,19 +434,11 @@ cgh_status cgh_ctx::forward_simt(const float *points, const float *A,
         tl.done();
     }
     {
-        static bool attr_set[64] = {};
-        if (device >= 0 && device < 64 && !attr_set[device]) {
-            cudaError_t e = cudaFuncSetAttribute(
-                simt_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                (int)SS_SMEM);
-            if (e != cudaSuccess) return cuda_fail(e, "FP32 GEMM attribute");
-            attr_set[device] = true;
-        }
         TimedLaunch tl(this, CGH_K_SIMT, s);
         const int vec_store = (Nx % 4 == 0) && (((uintptr_t)out & 15) == 0);
-        simt_gemm_kernel<<<(unsigned)(tiles * S), SS_THREADS, SS_SMEM, s>>>(
-            Lt, Rt, Npad, Nx, Ny, nxt, S, out, vec_store, part, count, d_status);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_simt_index(index, device, (unsigned)(tiles * S), s, Lt,
+                                          Rt, Npad, Nx, Ny, nxt, S, out, vec_store,
+                                          part, count, d_status);
         if (e != cudaSuccess) return cuda_fail(e, "FP32 GEMM launch");
         tl.done();
     }
