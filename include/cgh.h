@@ -250,6 +250,28 @@ typedef enum {
  * CGH_ERR_INVALID_ARG for a null handle or an unknown value. */
 cgh_status cgh_set_direct_schedule(cgh_handle h, int schedule);
 
+/* How the tensor-core GEMM of the separable forward methods (CGH_SEP_BF16,
+ * CGH_SEP_FP16, CGH_SEP_FP16X3) tiles its output (a scheduling choice of
+ * this implementation; the paper has no tensor-core form):
+ *   CGH_GEMM_SINGLE: one CTA per 128 x BN tile (BN = 112 or 128);
+ *   CGH_GEMM_PAIRS:  two CTAs of a cluster per 256 x BN tile, the MMAs
+ *                    issued for both SMs at once (tcgen05 cta_group::2), so
+ *                    that each SM loads half as many operand bytes per
+ *                    multiply-add;
+ *   CGH_GEMM_AUTO:   the build's default choice per shape.
+ * Every mode computes the same products with FP32 accumulation; results
+ * agree to rounding. */
+typedef enum {
+    CGH_GEMM_AUTO = 0,
+    CGH_GEMM_SINGLE = 1,
+    CGH_GEMM_PAIRS = 2
+} cgh_gemm_tiles;
+
+/* Select the GEMM tiling for later calls on this handle (also used by
+ * cgh_debug_gemm).  CGH_ERR_INVALID_ARG for a null handle or an unknown
+ * value. */
+cgh_status cgh_set_gemm_tiles(cgh_handle h, int tiles);
+
 /* Number of direct-kernel tile shapes compiled into this build, and the
  * i-th of them (0 <= i < count). */
 int cgh_direct_tile_count(void);

@@ -30,7 +30,7 @@ __all__ = [
     "cgh_launch_count", "cgh_status_string", "cgh_last_error",
     "cgh_debug_gemm", "CGHFunction", "default_handle", "KERNELS",
     "cgh_kernel_timing", "cgh_kernel_time", "cgh_tune_batch",
-    "cgh_kernel_timing_mask",
+    "cgh_kernel_timing_mask", "cgh_set_gemm_tiles", "GEMM_TILES",
 ]
 
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
@@ -86,6 +86,8 @@ def _load():
     L.cgh_direct_tile_get.argtypes = [ci, ctypes.POINTER(_Tile)]
     L.cgh_set_direct_tile.argtypes = [vp, ctypes.POINTER(_Tile)]
     L.cgh_set_direct_schedule.argtypes = [vp, ci]
+    L.cgh_set_gemm_tiles.argtypes = [vp, ci]
+    L.cgh_set_gemm_tiles.restype = ci
     L.cgh_tune.argtypes = [vp, ci, ci, ci, ci, vp, ctypes.POINTER(_Tile)]
     L.cgh_tune_batch.argtypes = [vp, ctypes.POINTER(_Problem), ci, ci, vp,
                                  ctypes.POINTER(_Tile)]
@@ -346,6 +348,17 @@ def cgh_set_direct_schedule(h, schedule="auto"):
     stage) units, split tiles summed in a fixed order) or "auto"."""
     st = _L().cgh_set_direct_schedule(h, SCHEDULES[schedule])
     _check(h, st, "cgh_set_direct_schedule")
+
+
+GEMM_TILES = {"auto": 0, "single": 1, "pairs": 2}
+
+
+def cgh_set_gemm_tiles(h, tiles="auto"):
+    """Tiling of the separable methods' tensor-core GEMM: "single" (one CTA
+    per 128-row tile), "pairs" (two CTAs of a cluster per 256-row tile,
+    tcgen05 cta_group::2) or "auto"."""
+    st = _L().cgh_set_gemm_tiles(h, GEMM_TILES[tiles])
+    _check(h, st, "cgh_set_gemm_tiles")
 
 
 def cgh_tune(h, N: int, Nx: int, Ny: int, method="direct", stream=None):

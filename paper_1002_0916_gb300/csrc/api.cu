@@ -360,6 +360,10 @@ cgh_status cgh_create(cgh_handle *out, int device) {
     h->load_tune_cache();
     if (const char *f = getenv("CGH_FAIL_ALLOC_AFTER")) h->fail_alloc_after = atoi(f);
     if (const char *f = getenv("CGH_SIMT_STAGE")) h->simt_stage = atoi(f);
+    if (const char *f = getenv("CGH_GEMM_TILES")) {
+        const int v = atoi(f);
+        if (v >= CGH_GEMM_AUTO && v <= CGH_GEMM_PAIRS) h->gemm_tiles = v;
+    }
     if (const char *f = getenv("CGH_BWD_POLY")) {
         const int v = atoi(f);
         if (v == 0 || v == 4 || v == 6) h->bwd_poly = v;
@@ -532,6 +536,14 @@ cgh_status cgh_set_direct_schedule(cgh_handle h, int schedule) {
         schedule != CGH_SCHED_SPLIT)
         return h->fail(CGH_ERR_INVALID_ARG, "unknown direct schedule %d", schedule);
     h->direct_schedule = schedule;
+    return CGH_OK;
+}
+
+cgh_status cgh_set_gemm_tiles(cgh_handle h, int tiles) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    if (tiles != CGH_GEMM_AUTO && tiles != CGH_GEMM_SINGLE && tiles != CGH_GEMM_PAIRS)
+        return h->fail(CGH_ERR_INVALID_ARG, "unknown GEMM tiling %d", tiles);
+    h->gemm_tiles = tiles;
     return CGH_OK;
 }
 

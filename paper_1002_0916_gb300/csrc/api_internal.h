@@ -63,6 +63,7 @@ struct cgh_ctx {
 
     int forced_tile = -1;                         // direct tile override
     int direct_schedule = CGH_SCHED_AUTO;         // cgh_set_direct_schedule
+    int gemm_tiles = CGH_GEMM_AUTO;               // cgh_set_gemm_tiles
     // polynomial (FMA-pipe) sin/cos columns of the direct adjoint's 16-column
     // strips: 0, 4 (default) or 6; CGH_BWD_POLY at cgh_create
     int bwd_poly = 4;

@@ -223,8 +223,14 @@ struct GemmOperands {
     float lo_scale;
     float *D;
     long long ldd;
+    int tiles = CGH_GEMM_AUTO;  // a cgh_gemm_tiles value
 };
 bool gemm_operands_ok(const GemmOperands &op);
+// umma2.cu: the same product on CTA pairs (256-row tiles over two SMs);
+// bnp = columns of a pair tile (one of the compiled widths)
+int pick_pair_n(int M, int N, int sms);
+cudaError_t launch_umma_pair(const GemmOperands &op, int bnp, unsigned *status,
+                             cudaStream_t s);
 cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
                              cudaStream_t s);
 // Split GEMM whose epilogue reduces the adjoint sums over its columns into

@@ -131,6 +131,7 @@ cgh_status cgh_ctx::forward_separable(const float *points, const float *A,
     op.lo_scale = 1.0f / LO_SCALE;
     op.D = out;
     op.ldd = Nx;
+    op.tiles = gemm_tiles;
     {
         TimedLaunch tl(this, CGH_K_GEMM, s);
         cudaError_t e = launch_umma_gemm(op, d_status, s);
@@ -156,6 +157,7 @@ extern "C" cgh_status cgh_debug_gemm(cgh_handle h, const void *A, const void *B,
     op.split = false;
     op.lo_scale = 0.0f;
     op.D = D;
+    op.tiles = h->gemm_tiles;
     op.ldd = N;
     if (!A || !B || !D || K % 64 != 0 || !gemm_operands_ok(op))
         return h->fail(CGH_ERR_INVALID_ARG,

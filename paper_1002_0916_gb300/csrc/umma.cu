@@ -351,6 +351,11 @@ static bool make_map(CUtensorMap *m, const void *base, long long inner,
     return r == CUDA_SUCCESS;
 }
 
+bool make_gemm_map(CUtensorMap *m, const void *base, long long inner, long long rows,
+                   long long ld, int box_rows, bool bf16) {
+    return make_map(m, base, inner, rows, ld, box_rows, bf16);
+}
+
 template <int BN, bool SPLIT, int STAGES, int MODE>
 static cudaError_t launch_gemm_t(const GemmOperands &op, const AdjEpiArgs &ea,
                                  unsigned *status, cudaStream_t s) {
@@ -426,7 +431,15 @@ cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
                              cudaStream_t s) {
     if (!gemm_operands_ok(op)) return cudaErrorInvalidValue;
     AdjEpiArgs ea{};
-    const int bn = pick_tile_n(op.M, op.N, sm_count_of_current_device());
+    const int sms = sm_count_of_current_device();
+    // CTA pairs halve each SM's operand bytes per multiply-add; measured on
+    // the 3840 x 2160 x 16384 product 1.9x (single pass) and 1.3x (split)
+    // faster than one-CTA tiles, equal at 1920 x 1024 x 1024.  A frame of
+    // at most 128 rows would leave half of every pair tile empty.
+    const bool pairs = op.tiles == CGH_GEMM_PAIRS ||
+                       (op.tiles == CGH_GEMM_AUTO && op.M > 128);
+    if (pairs) return launch_umma_pair(op, pick_pair_n(op.M, op.N, sms), status, s);
+    const int bn = pick_tile_n(op.M, op.N, sms);
     if (op.split)
         return bn == 112 ? launch_gemm_t<112, true, 3, 0>(op, ea, status, s)
                          : launch_gemm_t<128, true, 3, 0>(op, ea, status, s);

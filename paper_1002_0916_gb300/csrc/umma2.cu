@@ -1,0 +1,428 @@
+// umma2.cu -- the forward GEMM of the separable methods on CTA pairs
+// (tcgen05 cta_group::2): the same product as umma.cu,
+//
+//     D[m][n] = sum_k A[m][k] B[n][k]                      (single pass)
+//     D[m][n] = sum_k Ahi Bhi + s * (Ahi Blo + Alo Bhi)    (split, s = 2^-12)
+//
+// but each MMA covers a 256 x BNP tile computed by two SMs together.  The
+// two CTAs of a cluster each stage their own 128 rows of A and their own
+// half (BNP / 2 rows) of B; one thread of the even CTA issues the MMAs, which
+// read both CTAs' shared memory and write each CTA's 128 rows of D into that
+// CTA's tensor memory.  Per SM this moves half the operand bytes per
+// multiply-add of the one-CTA kernel at the same shared-memory footprint
+// (the one-CTA 128 x BN kernel loads 128 + BN rows per 128 BN outputs; a
+// pair loads 128 + BNP / 2 per SM for 128 BNP).
+//
+// Synchronisation (every wait bounded, as in umma.cu):
+//   * both CTAs' TMA loads of a stage complete on the even CTA's `full`
+//     barrier (the odd CTA's loads signal it across the pair, cta_group::2),
+//     whose expected byte count covers both halves; the MMA issuer waits on
+//     it alone;
+//   * the MMA issuer's commits arrive on the `empty` barriers and, at the
+//     end, the accumulator barrier of both CTAs (multicast commit);
+//   * cluster barriers after set-up (all barriers initialised, tensor memory
+//     allocated in both CTAs) and before the tensor memory is released.
+#include <cudaTypedefs.h>
+#include <stdlib.h>
+
+#include "api_internal.h"
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace cgh {
+namespace umma2 {
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Shared-memory address of `p` in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(const void *p, uint32_t rank) {
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(out)
+                 : "r"(smem_u32(p)), "r"(rank));
+    return out;
+}
+
+// Every thread of both CTAs.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile(
+        "barrier.cluster.arrive.release.aligned;\n"
+        "barrier.cluster.wait.acquire.aligned;" ::
+            : "memory");
+}
+
+// A wait whose phase may be completed by the other CTA's arrive: acquire at
+// cluster scope.  Bounded like mbar_wait_bounded.
+__device__ __forceinline__ bool try_wait_cluster(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool wait_cluster_bounded(uint64_t *bar, uint32_t parity) {
+    if (try_wait_cluster(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!try_wait_cluster(bar, parity))
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+    return true;
+}
+
+// Tensor memory of a CTA pair: one warp of each CTA, collectively.
+__device__ __forceinline__ void tmem_alloc2(uint32_t *dst_smem, uint32_t ncols) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+            smem_u32(dst_smem)),
+        "r"(ncols)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish2() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::
+                     : "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(ncols)
+                 : "memory");
+}
+
+// One 256 x N x 16 step of the pair, issued by one thread of the even CTA.
+__device__ __forceinline__ void mma2_f16(uint32_t d_tmem, uint64_t adesc,
+                                         uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive once on `bar` (same offset) in every CTA of `mask` when the MMAs
+// issued so far by this thread have completed.
+__device__ __forceinline__ void commit2(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster."
+        "multicast::cluster.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+// 2-D tiled load into this CTA's shared memory whose completion (bytes) is
+// signalled on the mbarrier at cluster address `bar`, which may lie in the
+// other CTA of the pair.  c0 * element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map,
+                                                 int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes."
+        "cta_group::2 [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+}  // namespace umma2
+
+template <int BNP, bool SPLIT, int STAGES>
+struct PairShape {
+    static constexpr int BM = 128, BK = 64, BNH = BNP / 2;
+    static constexpr uint32_t A_BYTES = BM * BK * 2;
+    static constexpr uint32_t B_BYTES = BNH * BK * 2;
+    static constexpr uint32_t STAGE_BYTES =
+        SPLIT ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
+    static constexpr uint32_t ACC1 = BNP <= 128 ? 128 : 256;
+    static constexpr uint32_t ACC_COLS = SPLIT ? ACC1 + BNP : BNP;
+    static constexpr uint32_t TMEM_COLS =
+        ACC_COLS <= 32 ? 32 : ACC_COLS <= 64 ? 64 : ACC_COLS <= 128 ? 128
+        : ACC_COLS <= 256 ? 256 : 512;
+    static constexpr int CH = BNP % 32 == 0 ? 32 : 16;
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+    static_assert(BNH % 8 == 0, "each B half is whole 8-row swizzle atoms");
+    static_assert(BNP % 16 == 0 && BNP >= 32 && BNP <= 256, "UMMA N at M = 256");
+    static_assert(ACC_COLS <= 512, "TMEM");
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+struct PairArgs {
+    int M, N, K;
+    float *D;
+    long long ldd;
+    float lo_scale;
+    unsigned *status;
+};
+
+// Grid: x = 2 x (column blocks of BNP), y = row blocks of 256; clusters of
+// two CTAs along x.
+template <int BNP, bool SPLIT, int STAGES>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
+                 const __grid_constant__ CUtensorMap tB,
+                 const __grid_constant__ CUtensorMap tA2,
+                 const __grid_constant__ CUtensorMap tB2, PairArgs g,
+                 uint32_t idesc) {
+    using S = PairShape<BNP, SPLIT, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[STAGES];   // (even CTA) both halves landed
+    __shared__ __align__(8) uint64_t empty[STAGES];
+    __shared__ __align__(8) uint64_t accum_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t rank = umma2::cluster_rank();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * 2 * S::BM + (int)rank * S::BM;  // this CTA's rows
+    const int np0 = (blockIdx.x >> 1) * BNP;                     // the pair's columns
+    const int nb = np0 + (int)rank * S::BNH;                     // this CTA's B rows
+    const int KB = (g.K + S::BK - 1) / S::BK;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&accum_bar, 1);
+        mbar_fence_init();
+        umma::prefetch_tmap(&tA);
+        umma::prefetch_tmap(&tB);
+        if (SPLIT) {
+            umma::prefetch_tmap(&tA2);
+            umma::prefetch_tmap(&tB2);
+        }
+    }
+    if (warp == 1) {
+        umma2::tmem_alloc2(&tmem_base, S::TMEM_COLS);
+        umma2::tmem_relinquish2();
+    }
+    umma::fence_before_sync();
+    umma2::cluster_sync();
+    umma::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------ producer (both CTAs)
+        int issued = 0;
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES &&
+                !mbar_wait_bounded(&empty[s], (uint32_t)(((kb / STAGES) - 1) & 1))) {
+                abort_flag = 1;
+                set_status(g.status, DEV_TIMEOUT);
+            }
+            if (abort_flag) break;
+            uint8_t *st = smem + (size_t)s * S::STAGE_BYTES;
+            // the even CTA's barrier counts the bytes of both CTAs' loads
+            if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * S::STAGE_BYTES);
+            const uint32_t bar = umma2::map_to_rank(&full[s], 0);
+            umma2::tma_load_2d_pair(st, &tA, kb * S::BK, m0, bar);
+            umma2::tma_load_2d_pair(st + S::A_BYTES, &tB, kb * S::BK, nb, bar);
+            if (SPLIT) {
+                umma2::tma_load_2d_pair(st + S::A_BYTES + S::B_BYTES, &tA2, kb * S::BK,
+                                        m0, bar);
+                umma2::tma_load_2d_pair(st + 2 * S::A_BYTES + S::B_BYTES, &tB2,
+                                        kb * S::BK, nb, bar);
+            }
+            ++issued;
+        }
+        if (abort_flag && rank == 0) {
+            // let the stages' copies land before shared memory goes: their
+            // barriers are here (the odd CTA cannot see its own loads'
+            // completion; it leaves only after the closing cluster barrier)
+            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+                mbar_wait_bounded(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
+        }
+    } else if (warp == 1 && lane == 0) {
+        if (rank == 0) {
+            // ---------------------------------------- MMA issuer (even CTA)
+            int done = 0;
+            for (int kb = 0; kb < KB; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t par = (uint32_t)((kb / STAGES) & 1);
+                if (!umma2::wait_cluster_bounded(&full[s], par)) {
+                    abort_flag = 1;
+                    set_status(g.status, DEV_TIMEOUT);
+                }
+                if (abort_flag) break;
+                umma::fence_after_sync();
+                const uint32_t a = smem_u32(smem + (size_t)s * S::STAGE_BYTES);
+                const uint32_t b = a + S::A_BYTES;
+                const uint64_t ad = umma::sw128_kmajor_desc(a);
+                const uint64_t bd = umma::sw128_kmajor_desc(b);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma2::mma2_f16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0);
+                if (SPLIT) {
+                    const uint32_t a2 = b + S::B_BYTES, b2 = a2 + S::A_BYTES;
+                    const uint64_t ad2 = umma::sw128_kmajor_desc(a2);
+                    const uint64_t bd2 = umma::sw128_kmajor_desc(b2);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma2::mma2_f16(tmem + S::ACC1, ad + 2 * kk, bd2 + 2 * kk, idesc,
+                                        (kb | kk) != 0);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma2::mma2_f16(tmem + S::ACC1, ad2 + 2 * kk, bd + 2 * kk, idesc, 1);
+                }
+                umma2::commit2(&empty[s], 0x3);
+                ++done;
+            }
+            // both CTAs' accumulators are complete -- or, after a timeout,
+            // only this CTA learns that its MMAs in flight have finished (the
+            // odd CTA's epilogue wait then runs out and skips its store)
+            umma2::commit2(&accum_bar, done == KB ? 0x3 : 0x1);
+        }
+    } else if (warp >= 2) {
+        // --------------------------------------- epilogue (both CTAs)
+        const int q = warp & 3;  // the 32-lane quarter of TMEM this warp reads
+        const int row = m0 + q * 32 + lane;
+        const bool ok = __all_sync(0xffffffffu, umma2::wait_cluster_bounded(&accum_bar, 0));
+        umma::fence_after_sync();
+        if (!ok) set_status(g.status, DEV_TIMEOUT);
+        if (ok && !abort_flag) {
+            const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
+            float *drow = g.D + (long long)row * g.ldd;
+            const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
+            constexpr int CH = S::CH;
+#pragma unroll 1
+            for (int c = 0; c < BNP; c += CH) {
+                uint32_t r[CH];
+                float v[CH];
+                if constexpr (CH == 32) umma::tmem_ld32(t_row + c, r);
+                else umma::tmem_ld16(t_row + c, r);
+                if (SPLIT) {
+                    uint32_t r2[CH];
+                    if constexpr (CH == 32) umma::tmem_ld32(t_row + S::ACC1 + c, r2);
+                    else umma::tmem_ld16(t_row + S::ACC1 + c, r2);
+                    umma::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < CH; ++i)
+                        v[i] = fmaf(g.lo_scale, __uint_as_float(r2[i]),
+                                    __uint_as_float(r[i]));
+                } else {
+                    umma::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < CH; ++i) v[i] = __uint_as_float(r[i]);
+                }
+                if (row < g.M) {
+                    const int col = np0 + c;
+                    if (vec && col + CH <= g.N) {
+#pragma unroll
+                        for (int i = 0; i < CH; i += 4)
+                            *reinterpret_cast<float4 *>(drow + col + i) =
+                                make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < CH; ++i)
+                            if (col + i < g.N) drow[col + i] = v[i];
+                    }
+                }
+            }
+        }
+    }
+    umma::fence_before_sync();
+    umma2::cluster_sync();  // no MMA, commit or relayed arrive still aims at either CTA
+    if (warp == 1) {
+        umma::fence_after_sync();
+        umma2::tmem_dealloc2(tmem, S::TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------- host side
+bool make_gemm_map(CUtensorMap *m, const void *base, long long inner, long long rows,
+                   long long ld, int box_rows, bool bf16);
+
+template <int BNP, bool SPLIT, int STAGES>
+static cudaError_t launch_pair_t(const GemmOperands &op, unsigned *status,
+                                 cudaStream_t s) {
+    using S = PairShape<BNP, SPLIT, STAGES>;
+    CUtensorMap tA, tB, tA2, tB2;
+    if (!make_gemm_map(&tA, op.A_hi, op.K, op.M, op.lda, S::BM, op.bf16) ||
+        !make_gemm_map(&tB, op.B_hi, op.K, op.N, op.ldb, S::BNH, op.bf16))
+        return cudaErrorInvalidValue;
+    if (SPLIT) {
+        if (!make_gemm_map(&tA2, op.A_lo, op.K, op.M, op.lda, S::BM, op.bf16) ||
+            !make_gemm_map(&tB2, op.B_lo, op.K, op.N, op.ldb, S::BNH, op.bf16))
+            return cudaErrorInvalidValue;
+    } else {
+        tA2 = tA;
+        tB2 = tB;
+    }
+    auto kern = umma_pair_kernel<BNP, SPLIT, STAGES>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(
+            kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    PairArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status};
+    dim3 grid(2 * ((op.N + BNP - 1) / BNP), (op.M + 2 * S::BM - 1) / (2 * S::BM));
+    const uint32_t idesc = umma::idesc_f16(2 * S::BM, BNP, op.bf16);
+    kern<<<grid, 192, S::SMEM, s>>>(tA, tB, tA2, tB2, g, idesc);
+    return cudaGetLastError();
+}
+
+// The pair widths compiled in (columns of one 256-row pair tile).
+static const int kPairBN[] = {112, 160, 224, 256};
+
+// Cost of a pair width: SM waves x columns per CTA (the work of one CTA is
+// proportional to its columns).
+static double pair_cost(int M, int N, int bnp, int sms) {
+    const long long ctas = 2LL * ((M + 255) / 256) * ((N + bnp - 1) / bnp);
+    return (double)((ctas + sms - 1) / sms) * bnp;
+}
+
+int pick_pair_n(int M, int N, int sms) {
+    int best = kPairBN[0];
+    double best_cost = 1e300;
+    for (int bnp : kPairBN) {
+        const double c = pair_cost(M, N, bnp, sms) / (1.0 + 0.002 * bnp);
+        if (c < best_cost) {
+            best_cost = c;
+            best = bnp;
+        }
+    }
+    return best;
+}
+
+// Stages: as many as fit in shared memory (the loads' latency is hidden by
+// the bytes in flight).
+cudaError_t launch_umma_pair(const GemmOperands &op, int bnp, unsigned *status,
+                             cudaStream_t s) {
+    static const int forced = [] {
+        const char *f = getenv("CGH_PAIR_BN");
+        return f ? atoi(f) : 0;
+    }();
+    if (forced) bnp = forced;
+    if (op.split) {
+        switch (bnp) {
+        case 112: return launch_pair_t<112, true, 4>(op, status, s);
+        case 160: return launch_pair_t<160, true, 4>(op, status, s);
+        case 224: return launch_pair_t<224, true, 3>(op, status, s);
+        case 256: return launch_pair_t<256, true, 3>(op, status, s);
+        }
+    } else {
+        switch (bnp) {
+        case 112: return launch_pair_t<112, false, 9>(op, status, s);
+        case 160: return launch_pair_t<160, false, 8>(op, status, s);
+        case 224: return launch_pair_t<224, false, 7>(op, status, s);
+        case 256: return launch_pair_t<256, false, 7>(op, status, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cgh

@@ -16,17 +16,27 @@ def cg():
     return cg
 
 
+@pytest.fixture(scope="module")
+def h(cg):
+    """A handle on the one-CTA tiling (the CTA-pair tiling has its own
+    tests)."""
+    handle = cg.cgh_create(0)
+    cg.cgh_set_gemm_tiles(handle, "single")
+    yield handle
+    cg.cgh_destroy(handle)
+
+
 @pytest.mark.parametrize("dtype", ["fp16", "bf16"])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 300, 128), (1, 1, 64),
                                    (129, 257, 192), (1024, 1920, 2048),
                                    (333, 129, 1024)])
-def test_gemm_matches_fp64_product(cg, dtype, M, N, K):
+def test_gemm_matches_fp64_product(cg, h, dtype, M, N, K):
     import torch
     tdt = {"fp16": torch.float16, "bf16": torch.bfloat16}[dtype]
     g = torch.Generator().manual_seed(M * 7 + N * 13 + K)
     A = torch.randn(M, K, generator=g).to(tdt)
     B = torch.randn(N, K, generator=g).to(tdt)
-    D = cg.cgh_debug_gemm(A.cuda(), B.cuda())
+    D = cg.cgh_debug_gemm(A.cuda(), B.cuda(), handle=h)
     torch.cuda.synchronize()
     A64 = A.double().numpy()
     B64 = B.double().numpy()
@@ -36,7 +46,7 @@ def test_gemm_matches_fp64_product(cg, dtype, M, N, K):
     assert np.all(err <= bound), float(np.max(err / bound))
 
 
-def test_gemm_structure_identity(cg):
+def test_gemm_structure_identity(cg, h):
     """A selects one column of B per row: catches transposed or shifted
     operand layouts exactly."""
     import torch
@@ -45,7 +55,7 @@ def test_gemm_structure_identity(cg):
     for m in range(M):
         A[m, (5 * m + 3) % K] = 1.0
     B = (torch.arange(N * K, dtype=torch.float32).reshape(N, K) % 2039).to(torch.float16)
-    D = cg.cgh_debug_gemm(A.cuda(), B.cuda()).cpu()
+    D = cg.cgh_debug_gemm(A.cuda(), B.cuda(), handle=h).cpu()
     ref = A.float() @ B.float().T
     assert torch.equal(D, ref)
 

@@ -23,9 +23,12 @@ def cg():
     return cg
 
 
-@pytest.fixture(scope="module")
-def h(cg):
+@pytest.fixture(scope="module", params=["auto", "single"])
+def h(cg, request):
+    """Every test on the default GEMM tiling (CTA pairs above 128 rows) and
+    on one-CTA tiles."""
     handle = cg.cgh_create(0)
+    cg.cgh_set_gemm_tiles(handle, request.param)
     yield handle
     cg.cgh_destroy(handle)
 
