@@ -321,9 +321,11 @@ static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
     const int Kp = pad_to(2 * N, 128);   // GEMM rows: whole 128-row tiles
     const int Npad = sep ? Kp / 2 : pad_to(N, BWD_THREADS);
     const int ldx = pad_to(Nx, 8), ldy = pad_to(Ny, 8);
-    const int Tx = sep ? (Nx + umma_tile_n() - 1) / umma_tile_n()
-                       : (Nx + BWD_STRIP - 1) / BWD_STRIP;
-    const int Ty = sep ? (Ny + umma_tile_n() - 1) / umma_tile_n() : Tx;
+    // partial-sum tiles: allocated for the narrowest GEMM column tile (128);
+    // the GEMM launches report the width they used
+    int Tx = sep ? (Nx + umma_tile_n() - 1) / umma_tile_n()
+                 : (Nx + BWD_STRIP - 1) / BWD_STRIP;
+    int Ty = sep ? (Ny + umma_tile_n() - 1) / umma_tile_n() : Tx;
     const size_t word_b = 256;
     const size_t rec_b = align256((size_t)Npad * sizeof(PointRec));
     const size_t px_b = align256((size_t)Tx * Npad * 3 * sizeof(float));
@@ -419,18 +421,24 @@ static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
         GemmOperands o2 = o1;
         o2.A_hi = Uhi; o2.A_lo = Ulo; o2.B_hi = Grh; o2.B_lo = Grl;
         o2.M = Kp; o2.N = Ny; o2.K = Nx; o2.lda = ldx; o2.ldb = ldx; o2.ldd = Ny;
+        o1.tiles = o2.tiles = h->gemm_tiles;
+        int wx = 128, wy = 128;  // column width of one partial-sum tile
         {
             TimedLaunch tl(h, CGH_K_BWD_GEMM, s);
-            e = launch_umma_adjoint(o1, rec, points, N, Npad, 0, part_x, h->d_status, s);
+            e = launch_umma_adjoint(o1, rec, points, N, Npad, 0, part_x, h->d_status, s,
+                                    &wx);
             if (e != cudaSuccess) return h->cuda_fail(e, "adjoint GEMM (x) launch");
             tl.done();
         }
         {
             TimedLaunch tl(h, CGH_K_BWD_GEMM, s);
-            e = launch_umma_adjoint(o2, rec, points, N, Npad, 1, part_y, h->d_status, s);
+            e = launch_umma_adjoint(o2, rec, points, N, Npad, 1, part_y, h->d_status, s,
+                                    &wy);
             if (e != cudaSuccess) return h->cuda_fail(e, "adjoint GEMM (y) launch");
             tl.done();
         }
+        Tx = (Nx + wx - 1) / wx;
+        Ty = (Ny + wy - 1) / wy;
     }
     {
         TimedLaunch tl(h, CGH_K_BWD_REDUCE, s);

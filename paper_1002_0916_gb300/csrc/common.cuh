@@ -231,14 +231,20 @@ bool gemm_operands_ok(const GemmOperands &op);
 int pick_pair_n(int M, int N, int sms);
 cudaError_t launch_umma_pair(const GemmOperands &op, int bnp, unsigned *status,
                              cudaStream_t s);
+struct AdjEpiArgs;
+cudaError_t launch_umma_pair_adjoint(const GemmOperands &op, const AdjEpiArgs &ea,
+                                     int sms, unsigned *status, cudaStream_t s,
+                                     int *tile_n);
 cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
                              cudaStream_t s);
 // Split GEMM whose epilogue reduces the adjoint sums over its columns into
-// part[n_tile][npad][3] (see umma.cu); rows are k = 2j + {0: cos, 1: sin}.
+// part[n_tile][npad][3] (see umma_epi.cuh); rows are k = 2j + {0: cos, 1:
+// sin}.  *tile_n receives the column width of one n_tile (128, or a CTA-pair
+// width >= 160), so part needs ceil(N / 128) tiles at most.
 cudaError_t launch_umma_adjoint(const GemmOperands &op, const PointRec *rec,
                                 const float *points, int npoints, int npad,
                                 int axis, float *part, unsigned *status,
-                                cudaStream_t s);
+                                cudaStream_t s, int *tile_n);
 int umma_tile_n();
 
 // separable.cu: U / V tables of the separable form.

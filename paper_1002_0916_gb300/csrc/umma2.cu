@@ -28,6 +28,7 @@
 #include "api_internal.h"
 #include "common.cuh"
 #include "umma.cuh"
+#include "umma_epi.cuh"
 
 namespace cgh {
 namespace umma2 {
@@ -153,23 +154,16 @@ struct PairShape {
     static_assert(SMEM <= 232448, "shared memory");
 };
 
-struct PairArgs {
-    int M, N, K;
-    float *D;
-    long long ldd;
-    float lo_scale;
-    unsigned *status;
-};
-
 // Grid: x = 2 x (column blocks of BNP), y = row blocks of 256; clusters of
-// two CTAs along x.
-template <int BNP, bool SPLIT, int STAGES>
+// two CTAs along x.  MODE 0: store D; MODE 1: the fused adjoint epilogue of
+// umma_epi.cuh over the pair's BNP columns (column tile blockIdx.x / 2).
+template <int BNP, bool SPLIT, int STAGES, int MODE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
 umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
                  const __grid_constant__ CUtensorMap tB,
                  const __grid_constant__ CUtensorMap tA2,
-                 const __grid_constant__ CUtensorMap tB2, PairArgs g,
-                 uint32_t idesc) {
+                 const __grid_constant__ CUtensorMap tB2, GemmArgs g,
+                 AdjEpiArgs ea, uint32_t idesc) {
     using S = PairShape<BNP, SPLIT, STAGES>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[STAGES];   // (even CTA) both halves landed
@@ -289,7 +283,10 @@ umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
         const bool ok = __all_sync(0xffffffffu, umma2::wait_cluster_bounded(&accum_bar, 0));
         umma::fence_after_sync();
         if (!ok) set_status(g.status, DEV_TIMEOUT);
-        if (ok && !abort_flag) {
+        if (MODE == 1 && ok && !abort_flag) {
+            adjoint_epilogue<BNP, SPLIT, S::ACC1>(tmem + ((uint32_t)(q * 32) << 16), row,
+                                                  np0, g, ea, lane, blockIdx.x >> 1);
+        } else if (ok && !abort_flag) {
             const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
             float *drow = g.D + (long long)row * g.ldd;
             const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
@@ -342,9 +339,9 @@ umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
 bool make_gemm_map(CUtensorMap *m, const void *base, long long inner, long long rows,
                    long long ld, int box_rows, bool bf16);
 
-template <int BNP, bool SPLIT, int STAGES>
+template <int BNP, bool SPLIT, int STAGES, int MODE = 0>
 static cudaError_t launch_pair_t(const GemmOperands &op, unsigned *status,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const AdjEpiArgs &ea = AdjEpiArgs{}) {
     using S = PairShape<BNP, SPLIT, STAGES>;
     CUtensorMap tA, tB, tA2, tB2;
     if (!make_gemm_map(&tA, op.A_hi, op.K, op.M, op.lda, S::BM, op.bf16) ||
@@ -358,7 +355,7 @@ static cudaError_t launch_pair_t(const GemmOperands &op, unsigned *status,
         tA2 = tA;
         tB2 = tB;
     }
-    auto kern = umma_pair_kernel<BNP, SPLIT, STAGES>;
+    auto kern = umma_pair_kernel<BNP, SPLIT, STAGES, MODE>;
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -368,10 +365,10 @@ static cudaError_t launch_pair_t(const GemmOperands &op, unsigned *status,
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    PairArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status};
+    GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status};
     dim3 grid(2 * ((op.N + BNP - 1) / BNP), (op.M + 2 * S::BM - 1) / (2 * S::BM));
     const uint32_t idesc = umma::idesc_f16(2 * S::BM, BNP, op.bf16);
-    kern<<<grid, 192, S::SMEM, s>>>(tA, tB, tA2, tB2, g, idesc);
+    kern<<<grid, 192, S::SMEM, s>>>(tA, tB, tA2, tB2, g, ea, idesc);
     return cudaGetLastError();
 }
 
@@ -423,6 +420,29 @@ cudaError_t launch_umma_pair(const GemmOperands &op, int bnp, unsigned *status,
         }
     }
     return cudaErrorInvalidValue;
+}
+
+// The adjoint GEMMs (split, fused epilogue) on CTA pairs: width from
+// {160, 224, 256} (the epilogue walks its columns 32 at a time); the column
+// tile width is returned in *tile_n (partial sums per tile of that width).
+cudaError_t launch_umma_pair_adjoint(const GemmOperands &op, const AdjEpiArgs &ea,
+                                     int sms, unsigned *status, cudaStream_t s,
+                                     int *tile_n) {
+    int best = 256;
+    double best_cost = 1e300;
+    for (int bnp : {160, 224, 256}) {
+        const double c = pair_cost(op.M, op.N, bnp, sms) / (1.0 + 0.002 * bnp);
+        if (c < best_cost) {
+            best_cost = c;
+            best = bnp;
+        }
+    }
+    *tile_n = best;
+    switch (best) {
+    case 160: return launch_pair_t<160, true, 4, 1>(op, status, s, ea);
+    case 224: return launch_pair_t<224, true, 3, 1>(op, status, s, ea);
+    default: return launch_pair_t<256, true, 3, 1>(op, status, s, ea);
+    }
 }
 
 }  // namespace cgh

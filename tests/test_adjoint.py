@@ -191,3 +191,27 @@ def test_deterministic_and_optional_outputs(cg, h):
         cg.cgh_backward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, Gd, method="naive",
                         handle=h)
     assert e.value.status == cg.CGH_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("case", [(300, 200, 150), (129, 130, 129), (4096, 1920, 1080)])
+def test_separable_adjoint_on_both_gemm_tilings(cg, oracle_mod, case):
+    """The split-FP16 adjoint on one-CTA GEMM tiles and on CTA pairs: both
+    within the bound of the FP64 gradient (sampled points at full size), and
+    within rounding of each other."""
+    N, Nx, Ny = case
+    c = make_cloud(N + 3, N, Nx, Ny, integer=False, zlo=0.3, zhi=1.2,
+                   lam=532e-9, p=6.4e-6)
+    G = grad_field(N + 9, Nx, Ny, scale=10.0)
+    sel = None if N <= 300 else np.sort(np.random.default_rng(5).choice(N, 32, replace=False))
+    ref = oracle_mod.grad(c, G.astype(np.float64), pts=sel)
+    got = {}
+    for tiles in ("single", "pairs"):
+        hh = cg.cgh_create(0)
+        try:
+            cg.cgh_set_gemm_tiles(hh, tiles)
+            got[tiles] = _bwd(cg, hh, c, G, "sep_fp16x3")
+        finally:
+            cg.cgh_destroy(hh)
+        _check_groups(got[tiles], ref, sel)
+    for a, b in zip(got["single"], got["pairs"]):
+        assert _rel(b, a) <= 1e-5
