@@ -258,7 +258,10 @@ cgh_status cgh_set_direct_schedule(cgh_handle h, int schedule);
  *                    issued for both SMs at once (tcgen05 cta_group::2), so
  *                    that each SM loads half as many operand bytes per
  *                    multiply-add;
- *   CGH_GEMM_AUTO:   the build's default choice per shape.
+ *   CGH_GEMM_AUTO:   CTA pairs for single holograms and adjoints of more
+ *                    than 128 rows, one-CTA tiles otherwise and for
+ *                    cgh_batch (whose persistent work list balances better
+ *                    with the smaller items).
  * Every mode computes the same products with FP32 accumulation; results
  * agree to rounding. */
 typedef enum {

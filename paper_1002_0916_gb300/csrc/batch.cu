@@ -561,7 +561,15 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
     }
     cgh_status st = ensure(bws, ws_bytes > 0 ? ws_bytes : 256, s, "batch workspace");
     if (st) return st;
-    cudaError_t e = prepare_umma_grouped();
+    // one-CTA items (128 x 128) unless CTA pairs were asked for: pair items
+    // (256 x 128) halve the number of work items, and on the 64-hologram
+    // batch the coarser balance cost more (4.55 ms) than the halved operand
+    // bytes per SM saved (one-CTA items: 4.24 ms)
+    const bool pairs = gemm_tiles == CGH_GEMM_PAIRS;
+    const int TM = pairs ? group_pair_tile_m() : 128;
+    const int BN = pairs ? group_pair_tile_n() : group_tile_n();
+    const int b_box = pairs ? group_pair_box_b() : group_tile_n();
+    cudaError_t e = pairs ? prepare_umma_grouped_pair() : prepare_umma_grouped();
     if (e != cudaSuccess) return cuda_fail(e, "grouped GEMM set-up");
     std::vector<GroupProb> gps(prep.size());
     std::vector<int> pidx;
@@ -593,7 +601,7 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
         op.lo_scale = 1.0f / LO_SCALE;
         op.D = probs[pidx[k]].out;
         op.ldd = sp.Nx;
-        if (!encode_group_prob(&gps[k], op))
+        if (!encode_group_prob(&gps[k], op, b_box))
             return fail(CGH_ERR_CUDA, "problem %d: tensor map encoding failed", pidx[k]);
     }
     // items: (problem, m tile, n tile), largest K first
@@ -602,9 +610,8 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int c) { return prep[a].Kp > prep[c].Kp; });
     std::vector<uint2> items;
-    const int BN = group_tile_n();
     for (int k : order)
-        for (int mt = 0; mt < (prep[k].Ny + 127) / 128; ++mt)
+        for (int mt = 0; mt < (prep[k].Ny + TM - 1) / TM; ++mt)
             for (int nt = 0; nt < (prep[k].Nx + BN - 1) / BN; ++nt)
                 items.push_back(make_uint2((unsigned)k, (unsigned)mt | ((unsigned)nt << 16)));
     const int nitems = (int)items.size();
@@ -625,6 +632,7 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
     const int method = CGH_SEP_FP16X3;
     key = fnv1a(key, &method, sizeof(method));
     key = fnv1a(key, &count, sizeof(count));
+    key = fnv1a(key, &pairs, sizeof(pairs));
     key = fnv1a(key, probs, sizeof(cgh_problem) * (size_t)count);
     int maxNpad = 1, max_blocks = 1;
     for (auto &sp : prep) {
@@ -654,7 +662,8 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
             d_prep);
         r = cudaGetLastError();
         if (r != cudaSuccess) return r;
-        return launch_umma_grouped(d_gp, d_items, nitems, d_status, sm_count, q);
+        return pairs ? launch_umma_grouped_pair(d_gp, d_items, nitems, d_status, sm_count, q)
+                     : launch_umma_grouped(d_gp, d_items, nitems, d_status, sm_count, q);
     };
     return run_batch_graph(key, meta_b, np ? 3 : 0, fill, enqueue, s, CGH_K_BATCH_SEP);
 }

@@ -556,12 +556,12 @@ umma_grouped_kernel(const GroupProb *__restrict__ probs,
 
 constexpr int GROUP_BN = 128, GROUP_STAGES = 3;
 
-bool encode_group_prob(GroupProb *gp, const GemmOperands &op) {
+bool encode_group_prob(GroupProb *gp, const GemmOperands &op, int b_box_rows) {
     if (!gemm_operands_ok(op) || !op.split) return false;
     if (!make_map(&gp->tA, op.A_hi, op.K, op.M, op.lda, 128, op.bf16) ||
-        !make_map(&gp->tB, op.B_hi, op.K, op.N, op.ldb, GROUP_BN, op.bf16) ||
+        !make_map(&gp->tB, op.B_hi, op.K, op.N, op.ldb, b_box_rows, op.bf16) ||
         !make_map(&gp->tA2, op.A_lo, op.K, op.M, op.lda, 128, op.bf16) ||
-        !make_map(&gp->tB2, op.B_lo, op.K, op.N, op.ldb, GROUP_BN, op.bf16))
+        !make_map(&gp->tB2, op.B_lo, op.K, op.N, op.ldb, b_box_rows, op.bf16))
         return false;
     gp->D = op.D;
     gp->ldd = op.ldd;

@@ -149,11 +149,22 @@ struct alignas(64) GroupProb {
 
 // Fill gp (tensor maps and sizes) for the split GEMM `op`; false if a
 // tensor map cannot be encoded.
-bool encode_group_prob(GroupProb *gp, const GemmOperands &op);
+// b_box_rows: rows of B per TMA box (the tile's columns for one-CTA items,
+// half of them for CTA-pair items)
+bool encode_group_prob(GroupProb *gp, const GemmOperands &op, int b_box_rows);
 cudaError_t launch_umma_grouped(const GroupProb *probs, const uint2 *items,
                                 int nitems, unsigned *status, int sm_count,
                                 cudaStream_t s);
 cudaError_t prepare_umma_grouped();
 int group_tile_n();
+// umma2.cu: the same on CTA pairs; items are (problem, 256-row tile,
+// group_pair_tile_n()-column tile)
+cudaError_t launch_umma_grouped_pair(const GroupProb *probs, const uint2 *items,
+                                     int nitems, unsigned *status, int sm_count,
+                                     cudaStream_t s);
+cudaError_t prepare_umma_grouped_pair();
+int group_pair_tile_m();
+int group_pair_tile_n();
+int group_pair_box_b();
 
 }  // namespace cgh

@@ -422,6 +422,240 @@ cudaError_t launch_umma_pair(const GemmOperands &op, int bnp, unsigned *status,
     return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------ grouped (batch), pairs
+// The persistent grouped split GEMM of the batch on CTA pairs: clusters of
+// two CTAs take work items (problem, 256-row tile, 128-column tile) round
+// robin; per SM 128 rows of A and 64 rows of B per stage.  Two TMEM
+// accumulator buffers (hi*hi and cross terms, 256 columns each) let the
+// epilogue of one item overlap the MMAs of the next.  The even CTA's
+// `acc_empty` barrier collects one arrival from each of the 8 epilogue warps
+// of the pair (the odd CTA's arrive remotely) before that buffer is reused.
+constexpr int GP_BN = 128, GP_STAGES = 4;
+
+__device__ __forceinline__ void remote_arrive(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(
+                     cluster_addr)
+                 : "memory");
+}
+
+template <int STAGES>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+umma_grouped_pair_kernel(const GroupProb *__restrict__ probs,
+                         const uint2 *__restrict__ items, int nitems,
+                         unsigned *status) {
+    using S = PairShape<GP_BN, true, STAGES>;
+    constexpr uint32_t ACC_COLS = 2 * GP_BN;        // hi*hi and cross terms
+    constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;    // two buffers
+    static_assert(TMEM_COLS <= 512, "TMEM");
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[STAGES];
+    __shared__ __align__(8) uint64_t empty[STAGES];
+    __shared__ __align__(8) uint64_t acc_full[2];
+    __shared__ __align__(8) uint64_t acc_empty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t rank = umma2::cluster_rank();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 8);  // 4 epilogue warps in each CTA
+        }
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        umma2::tmem_alloc2(&tmem_base, TMEM_COLS);
+        umma2::tmem_relinquish2();
+    }
+    umma::fence_before_sync();
+    umma2::cluster_sync();
+    umma::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ------------------------------------------ producer (both CTAs)
+        unsigned g = 0, issued_from = 0;
+        for (int it = cl; it < nitems && !abort_flag; it += ncl) {
+            const uint2 w = items[it];
+            const GroupProb *gp = probs + w.x;
+            const int m0 = (int)(w.y & 0xffffu) * 2 * S::BM + (int)rank * S::BM;
+            const int nb = (int)(w.y >> 16) * GP_BN + (int)rank * S::BNH;
+            const int KB = (gp->K + S::BK - 1) / S::BK;
+            for (int kb = 0; kb < KB; ++kb, ++g) {
+                const int s = (int)(g % STAGES);
+                if (g >= STAGES &&
+                    !mbar_wait_bounded(&empty[s], (uint32_t)(((g / STAGES) - 1) & 1))) {
+                    abort_flag = 1;
+                    set_status(status, DEV_TIMEOUT);
+                }
+                if (abort_flag) break;
+                uint8_t *st = smem + (size_t)s * S::STAGE_BYTES;
+                if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * S::STAGE_BYTES);
+                const uint32_t bar = umma2::map_to_rank(&full[s], 0);
+                umma2::tma_load_2d_pair(st, &gp->tA, kb * S::BK, m0, bar);
+                umma2::tma_load_2d_pair(st + S::A_BYTES, &gp->tB, kb * S::BK, nb, bar);
+                umma2::tma_load_2d_pair(st + S::A_BYTES + S::B_BYTES, &gp->tA2,
+                                        kb * S::BK, m0, bar);
+                umma2::tma_load_2d_pair(st + 2 * S::A_BYTES + S::B_BYTES, &gp->tB2,
+                                        kb * S::BK, nb, bar);
+                issued_from = g + 1;
+            }
+        }
+        if (abort_flag && rank == 0) {
+            const unsigned lo = issued_from > STAGES ? issued_from - STAGES : 0;
+            for (unsigned u = lo; u < issued_from; ++u)
+                mbar_wait_bounded(&full[u % STAGES], (uint32_t)((u / STAGES) & 1));
+        }
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+        // ---------------------------------------- MMA issuer (even CTA)
+        const uint32_t idesc = umma::idesc_f16(2 * S::BM, GP_BN, false);
+        unsigned g = 0;
+        int n = 0;
+        for (int it = cl; it < nitems && !abort_flag; it += ncl, ++n) {
+            const int b = n & 1;
+            if (!umma2::wait_cluster_bounded(&acc_empty[b],
+                                             (uint32_t)(((n >> 1) & 1) ^ 1))) {
+                abort_flag = 1;
+                set_status(status, DEV_TIMEOUT);
+                break;
+            }
+            umma::fence_after_sync();
+            const uint32_t d0 = tmem + (uint32_t)b * ACC_COLS, d1 = d0 + GP_BN;
+            const GroupProb *gp = probs + items[it].x;
+            const int KB = (gp->K + S::BK - 1) / S::BK;
+            bool ok = true;
+            for (int kb = 0; kb < KB; ++kb, ++g) {
+                const int s = (int)(g % STAGES);
+                if (!umma2::wait_cluster_bounded(&full[s], (uint32_t)((g / STAGES) & 1))) {
+                    abort_flag = 1;
+                    set_status(status, DEV_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint32_t a = smem_u32(smem + (size_t)s * S::STAGE_BYTES);
+                const uint32_t bb = a + S::A_BYTES;
+                const uint32_t a2 = bb + S::B_BYTES, b2 = a2 + S::A_BYTES;
+                const uint64_t ad = umma::sw128_kmajor_desc(a);
+                const uint64_t bd = umma::sw128_kmajor_desc(bb);
+                const uint64_t ad2 = umma::sw128_kmajor_desc(a2);
+                const uint64_t bd2 = umma::sw128_kmajor_desc(b2);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma2::mma2_f16(d0, ad + 2 * kk, bd + 2 * kk, idesc, (kb | kk) != 0);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma2::mma2_f16(d1, ad + 2 * kk, bd2 + 2 * kk, idesc, (kb | kk) != 0);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma2::mma2_f16(d1, ad2 + 2 * kk, bd + 2 * kk, idesc, 1);
+                umma2::commit2(&empty[s], 0x3);
+            }
+            // a timed-out item is not handed to the odd CTA's epilogue (its
+            // wait runs out); this CTA's epilogue learns that its MMAs ended
+            umma2::commit2(&acc_full[b], ok ? 0x3 : 0x1);
+        }
+    } else if (warp >= 2) {
+        // --------------------------------------- epilogue (both CTAs)
+        const int q = warp & 3;
+        const uint32_t lead_empty0 = umma2::map_to_rank(&acc_empty[0], 0);
+        int n = 0;
+        for (int it = cl; it < nitems; it += ncl, ++n) {
+            const int b = n & 1;
+            const bool ok = __all_sync(
+                0xffffffffu,
+                umma2::wait_cluster_bounded(&acc_full[b], (uint32_t)((n >> 1) & 1)));
+            umma::fence_after_sync();
+            if (!ok || abort_flag) {
+                if (!ok) set_status(status, DEV_TIMEOUT);
+                break;
+            }
+            const uint2 w = items[it];
+            const GroupProb *gp = probs + w.x;
+            const int m0 = (int)(w.y & 0xffffu) * 2 * S::BM + (int)rank * S::BM;
+            const int n0 = (int)(w.y >> 16) * GP_BN;
+            const int row = m0 + q * 32 + lane;
+            const int M = gp->M, Ncols = gp->N;
+            const long long ldd = gp->ldd;
+            const float los = gp->lo_scale;
+            float *drow = gp->D + (long long)row * ldd;
+            const bool vec = ((ldd & 3) == 0) && ((((uintptr_t)gp->D) & 15) == 0);
+            const uint32_t t_row =
+                tmem + (uint32_t)b * ACC_COLS + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < GP_BN; c += 32) {
+                uint32_t r[32], r2[32];
+                umma::tmem_ld32(t_row + c, r);
+                umma::tmem_ld32(t_row + GP_BN + c, r2);
+                umma::tmem_ld_wait();
+                float v[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    v[i] = fmaf(los, __uint_as_float(r2[i]), __uint_as_float(r[i]));
+                if (row < M) {
+                    const int col = n0 + c;
+                    if (vec && col + 32 <= Ncols) {
+#pragma unroll
+                        for (int i = 0; i < 32; i += 4)
+                            *reinterpret_cast<float4 *>(drow + col + i) =
+                                make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (col + i < Ncols) drow[col + i] = v[i];
+                    }
+                }
+            }
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) remote_arrive(lead_empty0 + (uint32_t)b * 8u);
+        }
+    }
+    umma::fence_before_sync();
+    umma2::cluster_sync();
+    if (warp == 1) {
+        umma::fence_after_sync();
+        umma2::tmem_dealloc2(tmem, TMEM_COLS);
+    }
+}
+
+cudaError_t prepare_umma_grouped_pair() {
+    using S = PairShape<GP_BN, true, GP_STAGES>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && attr_set[dev]) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(umma_grouped_pair_kernel<GP_STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::SMEM);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) attr_set[dev] = true;
+    return e;
+}
+
+cudaError_t launch_umma_grouped_pair(const GroupProb *probs, const uint2 *items,
+                                     int nitems, unsigned *status, int sm_count,
+                                     cudaStream_t s) {
+    using S = PairShape<GP_BN, true, GP_STAGES>;
+    if (nitems <= 0) return cudaSuccess;
+    const int clusters = nitems < sm_count / 2 ? nitems : sm_count / 2;
+    umma_grouped_pair_kernel<GP_STAGES><<<2 * (clusters > 0 ? clusters : 1), 192,
+                                          S::SMEM, s>>>(probs, items, nitems, status);
+    return cudaGetLastError();
+}
+
+int group_pair_tile_m() { return 2 * 128; }
+int group_pair_tile_n() { return GP_BN; }
+int group_pair_box_b() { return GP_BN / 2; }
+
 // The adjoint GEMMs (split, fused epilogue) on CTA pairs: width from
 // {160, 224, 256} (the epilogue walks its columns 32 at a time); the column
 // tile width is returned in *tile_n (partial sums per tile of that width).

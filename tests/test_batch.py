@@ -165,3 +165,38 @@ def test_tune_batch(cg, h):
     cg.cgh_batch(probs, handle=h)
     torch.cuda.synchronize()
     assert cg.cgh_last_device_status(h) == cg.CGH_OK
+
+
+@pytest.mark.parametrize("tiles", ["single", "pairs"])
+def test_sep_batch_on_both_gemm_tilings(cg, oracle_mod, tiles):
+    """The separable batch on one-CTA items (128 x 128) and on CTA-pair items
+    (256 x 128): every hologram of an uneven small batch within the split-FP16
+    bound of the FP64 oracle, and the two tilings within rounding of each
+    other; a second call of the same geometry replays the graph and gives
+    the same bits."""
+    import torch
+    clouds = _small_clouds()
+    out = {}
+    for t in ("single", "pairs"):
+        hh = cg.cgh_create(0)
+        try:
+            cg.cgh_set_gemm_tiles(hh, t)
+            probs = _problems(clouds)
+            cg.cgh_batch(probs, method="sep_fp16x3", handle=hh)
+            torch.cuda.synchronize()
+            first = [p["out"].cpu().numpy() for p in probs]
+            cg.cgh_batch(probs, method="sep_fp16x3", handle=hh)
+            torch.cuda.synchronize()
+            assert cg.cgh_last_device_status(hh) == cg.CGH_OK
+            out[t] = [p["out"].cpu().numpy() for p in probs]
+            for a, b in zip(first, out[t]):
+                assert np.array_equal(a, b)
+        finally:
+            cg.cgh_destroy(hh)
+    for c, got in zip(clouds, out[tiles]):
+        if c.N == 0:
+            assert np.count_nonzero(got) == 0
+            continue
+        assert rel_rms(got, oracle_mod.forward(c)) <= 1e-4
+    for a, b in zip(out["single"], out["pairs"]):
+        assert np.max(np.abs(a - b)) <= 1e-6 * max(1.0, float(np.max(np.abs(b))))
