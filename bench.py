@@ -198,6 +198,35 @@ def cpu_baseline(cloud, seconds: float):
                       f"FP64 Eq. 1, OpenMP over rows; {dt:.2f} s"}
 
 
+def cpu_eq2_table1(seconds: float):
+    """The paper's CPU method beside Table 1's CPU column: the oracle's Eq. 2
+    recurrence (FP64, one host core), timed on a few evenly spaced rows of
+    each Table 1 hologram and scaled to the whole frame."""
+    import numpy as np
+
+    import oracle
+    from workloads import TABLE1_POINTS, table1_cloud
+    oracle.build()
+    per_n = seconds / len(TABLE1_POINTS)
+    ms, sample = [], None
+    for n in TABLE1_POINTS:
+        c = table1_cloud(n)
+        probe = np.array([c.Ny // 2], dtype=np.int32)
+        t0 = time.perf_counter()
+        oracle.forward_recurrence(c, rows=probe, nthreads=1)
+        per_row = time.perf_counter() - t0
+        k = int(max(1, min(c.Ny, per_n / max(per_row, 1e-6))))
+        rows = np.unique(np.linspace(0, c.Ny - 1, k).round().astype(np.int32))
+        t0 = time.perf_counter()
+        oracle.forward_recurrence(c, rows=rows, nthreads=1)
+        dt = time.perf_counter() - t0
+        ms.append(1e3 * dt / len(rows) * c.Ny)
+        sample = f"{len(rows)} evenly spaced rows per hologram"
+    return {"N": list(TABLE1_POINTS), "ms_whole_frame": ms, "cores": 1,
+            "kind": "oracle Eq. 2 recurrence (FP64)",
+            "sample": f"{sample}, scaled to 1024 rows"}
+
+
 # -------------------------------------------------------------- reference
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -621,6 +650,8 @@ def run_ours(args):
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline and args.workload == "paper":
             line["cpu_baseline"] = cpu_baseline(c, args.cpu_seconds)
+        if world == 1 and not args.no_cpu_baseline and args.workload == "table1":
+            line["table1"]["cpu_eq2_one_core"] = cpu_eq2_table1(args.cpu_seconds)
         print(json.dumps(line), flush=True)
     return 0
 
