@@ -51,11 +51,15 @@ struct SimtStage {
     static_assert((L * 4) % 16 == 0 && (R * 4) % 16 == 0, "bulk sizes");
     static_assert(SS_KPAD % BK == 0, "K padding covers the stage");
 };
-// The shapes compiled in: (BK, NST).  Measured on the 1920x1024x1024 and
-// 3840x2160x16384 frames, (32, 2) was fastest (fewest barriers per
-// multiply-add at two CTAs per SM); (16, 4) within 3%, (8, 8) and (32, 3)
-// (one CTA per SM) 6-12% slower.
-#define CGH_SIMT_STAGES(X) X(16, 4) X(32, 2) X(8, 8) X(32, 3)
+// The shapes compiled in: (BK, NST, PK): PK 1 = fma.rn.f32x2 pairs, two
+// CTAs per SM (128 registers); 0 = scalar FMAs; 2 = pairs, one CTA per SM
+// (up to 255 registers, room to load the next k's operands early).
+// Measured on the 1920x1024x1024 and 3840x2160x16384 frames, (32, 2, 1)
+// was fastest (fewest barriers per multiply-add at two CTAs per SM);
+// (16, 4, 1) within 3%; (8, 8, 1), (32, 3, 1) (one CTA per SM), scalar FMAs
+// (32, 2, 0: 5-7%) and (32, 4, 2) (8-16%) slower.  The last two are not
+// compiled in.
+#define CGH_SIMT_STAGES(X) X(16, 4, 1) X(32, 2, 1) X(8, 8, 1) X(32, 3, 1)
 
 // Position of R value (row i of the tile, copy d) in a doubled R row of
 // 2 * SS_BM floats.  Row i = wy 64 + h 32 + ty 4 + q (warp row wy, half h,
@@ -137,8 +141,8 @@ __device__ __forceinline__ void ss_issue(float *smem, uint64_t *full,
 
 // One unit = (tile, k slice).  Units are numbered tile-major: unit =
 // tile * S + slice.  Tiles are row-major over (x tile, y tile).
-template <int BK, int NST>
-__global__ void __launch_bounds__(SS_THREADS, 2)
+template <int BK, int NST, int PK>
+__global__ void __launch_bounds__(SS_THREADS, PK == 2 ? 1 : 2)
 simt_gemm_kernel(const float *__restrict__ Lt, const float *__restrict__ Rt,
                  int Npad, int Nx, int Ny, int nxt, int S,
                  float *__restrict__ out, int vec_store,
@@ -219,10 +223,21 @@ simt_gemm_kernel(const float *__restrict__ Lt, const float *__restrict__ Rt,
                                      make_float2(r1.x, r1.y), make_float2(r1.z, r1.w),
                                      make_float2(r2.x, r2.y), make_float2(r2.z, r2.w),
                                      make_float2(r3.x, r3.y), make_float2(r3.z, r3.w)};
+                if constexpr (PK) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                    for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[i][c] = __ffma2_rn(r[i], l[c], acc[i][c]);
+                        for (int c = 0; c < 4; ++c)
+                            acc[i][c] = __ffma2_rn(r[i], l[c], acc[i][c]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            acc[i][c].x = fmaf(r[i].x, l[c].x, acc[i][c].x);
+                            acc[i][c].y = fmaf(r[i].x, l[c].y, acc[i][c].y);
+                        }
+                }
             }
         }
         __syncthreads();  // every thread is done with slot s
@@ -329,7 +344,7 @@ struct SimtPlan {
 
 static SimtPlan simt_plan(int index) {
     int i = 0;
-#define X(bk, ns)                                                               \
+#define X(bk, ns, pk)                                                           \
     if (index == i)                                                             \
         return SimtPlan{bk, ns,                                                 \
                         SimtStage<bk, ns>::SMEM <= 110 * 1024 ? 2 : 1};         \
@@ -341,13 +356,13 @@ static SimtPlan simt_plan(int index) {
 
 int simt_stage_count() {
     int n = 0;
-#define X(bk, ns) ++n;
+#define X(bk, ns, pk) ++n;
     CGH_SIMT_STAGES(X)
 #undef X
     return n;
 }
 
-template <int BK, int NST>
+template <int BK, int NST, int PK>
 static cudaError_t launch_simt_gemm(int device, unsigned grid, cudaStream_t s,
                                     const float *Lt, const float *Rt, int Npad,
                                     int Nx, int Ny, int nxt, int S, float *out,
@@ -356,13 +371,13 @@ static cudaError_t launch_simt_gemm(int device, unsigned grid, cudaStream_t s,
     using G = SimtStage<BK, NST>;
     static bool attr_set[64] = {};
     if (device < 0 || device >= 64 || !attr_set[device]) {
-        cudaError_t e = cudaFuncSetAttribute(simt_gemm_kernel<BK, NST>,
+        cudaError_t e = cudaFuncSetAttribute(simt_gemm_kernel<BK, NST, PK>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)G::SMEM);
         if (e != cudaSuccess) return e;
         if (device >= 0 && device < 64) attr_set[device] = true;
     }
-    simt_gemm_kernel<BK, NST><<<grid, SS_THREADS, G::SMEM, s>>>(
+    simt_gemm_kernel<BK, NST, PK><<<grid, SS_THREADS, G::SMEM, s>>>(
         Lt, Rt, Npad, Nx, Ny, nxt, S, out, vec_store, part, count, status);
     return cudaGetLastError();
 }
@@ -374,11 +389,11 @@ static cudaError_t launch_simt_index(int index, int device, unsigned grid,
                                      float *part, unsigned *count,
                                      unsigned *status) {
     int i = 0;
-#define X(bk, ns)                                                               \
+#define X(bk, ns, pk)                                                           \
     if (index == i)                                                             \
-        return launch_simt_gemm<bk, ns>(device, grid, s, Lt, Rt, Npad, Nx, Ny,  \
-                                        nxt, S, out, vec_store, part, count,    \
-                                        status);                                \
+        return launch_simt_gemm<bk, ns, pk>(device, grid, s, Lt, Rt, Npad, Nx,  \
+                                            Ny, nxt, S, out, vec_store, part,   \
+                                            count, status);                     \
     ++i;
     CGH_SIMT_STAGES(X)
 #undef X
