@@ -115,10 +115,16 @@ cgh_status cgh_forward(cgh_handle h, const float *points, const float *A,
                        const float *z, int N, double lambda, double p,
                        int Nx, int Ny, float *out, int method, void *stream);
 
-/* cgh_forward from HOST buffers: copies points, A, z to the handle's
- * workspace, computes, copies the hologram back into out_host (Ny*Nx
- * floats) and synchronises the stream before returning.  Pinned host
- * memory gives the fastest copies; pageable memory works too. */
+/* cgh_forward from HOST buffers (Ny*Nx floats out), synchronising the
+ * stream before returning.  Page-locked host buffers that are mapped into
+ * the device's address space (cudaHostAlloc / cudaHostRegister memory,
+ * e.g. PyTorch pinned tensors, on a unified-addressing system) are used in
+ * place: the kernels read such inputs over the host link, and the methods
+ * that store the hologram tile by tile as they run (CGH_DIRECT_FP32,
+ * CGH_RECUR_FP32, CGH_NAIVE_FP32, CGH_SEP_FP32) write such an output there
+ * directly.  The tensor-core methods, and any other buffer (pageable
+ * memory, device memory), go through the handle's workspace and one copy.
+ * The result is the same either way. */
 cgh_status cgh_forward_host(cgh_handle h, const float *points_host,
                             const float *A_host, const float *z_host, int N,
                             double lambda, double p, int Nx, int Ny,

@@ -90,3 +90,27 @@ def test_forward_captured_in_caller_graph(cg, h, oracle_mod, method):
         torch.cuda.synchronize()
         _check(c, out.cpu().numpy(), oracle_mod.forward(c), method)
     assert cg.cgh_last_device_status(h) == cg.CGH_OK
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_host_entry_point_buffer_kinds(cg, h, method):
+    """cgh_forward_host with pinned (mapped, used in place) and pageable
+    (staged) host buffers, in every combination of inputs and output: the
+    same hologram as the device-buffer call, bit for bit."""
+    import torch
+    c = make_cloud(77, 120, 201, 97, integer=False, zlo=0.2, zhi=0.9, lam=532e-9,
+                   p=8e-6)
+    pts, A, z = to_dev(c)
+    ref = cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, method=method, handle=h)
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)) for a in (c.xy, c.A, c.z)]
+    for pin_in in (False, True):
+        ins = [t.pin_memory() if pin_in else t.clone() for t in host_in]
+        for pin_out in (False, True):
+            out = torch.full((c.Ny, c.Nx), float("nan"))
+            if pin_out:
+                out = out.pin_memory()
+            cg.cgh_forward_host(*ins, c.lam, c.p, c.Nx, c.Ny, out=out, method=method,
+                                handle=h)
+            assert np.array_equal(out.numpy(), ref), (method, pin_in, pin_out)
