@@ -36,7 +36,7 @@ def main():
         pts, A, z = to_dev(c)
         rows = None if nrows is None else sample_rows(c.Ny, nrows)
         ref = oracle.forward(c, rows=rows)
-        for m in ("direct", "sep_fp16x3", "sep_fp16", "sep_bf16"):
+        for m in ("direct", "recur", "sep_fp32", "sep_fp16x3", "sep_fp16", "sep_bf16"):
             I = cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, method=m, handle=h)
             torch.cuda.synchronize()
             got = I.cpu().numpy()

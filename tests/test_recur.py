@@ -122,7 +122,7 @@ def test_cfg5_continuous_sampled_rows(cg, h, oracle_mod):
     assert err <= TOL * sum_abs_A(c), err
 
 
-@pytest.mark.parametrize("method", ["direct", "recur", "sep_fp16x3"])
+@pytest.mark.parametrize("method", ["direct", "recur", "sep_fp32", "sep_fp16x3"])
 def test_table1_largest_point_count(cg, h, oracle_mod, method):
     """1920 x 1024 pixels from 3584 points, the last row of the paper's
     Table 1, in the configuration the Table 1 sweep of the benchmark runs."""
