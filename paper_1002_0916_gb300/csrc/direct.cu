@@ -130,6 +130,8 @@ direct_fwd_kernel(const float *__restrict__ phx, const float *__restrict__ phy,
                        phy + (size_t)yt * Npad * TY + (size_t)s0 * S::SY,
                        amp + (size_t)s0 * PT, s1 - s0, 0u, acc, status))
         return;
+    // only the stores are left: the next kernel of the stream may launch
+    pdl_trigger();
     if (q < 0) {
         L::store(acc, smem, xt, yt, Nx, Ny, out, vec_store);
         return;

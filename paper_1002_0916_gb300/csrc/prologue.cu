@@ -21,6 +21,7 @@ __global__ void prologue_kernel(const float *__restrict__ points,
                                 double lambda, double p,
                                 PointRec *__restrict__ rec,
                                 unsigned *status) {
+    pdl_wait();  // the inputs may come from the kernel before
     pdl_trigger();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Npad) return;
@@ -36,9 +37,8 @@ cudaError_t launch_prologue(const float *points, const float *A,
     // the points thinly over many SMs
     int threads = 32;
     int blocks = (Npad + threads - 1) / threads;
-    prologue_kernel<<<blocks, threads, 0, s>>>(points, A, z, N, Npad, lambda,
-                                                p, rec, status);
-    return cudaGetLastError();
+    return launch_dependent(prologue_kernel, dim3(blocks), dim3(threads), 0, s, points,
+                            A, z, N, Npad, lambda, p, rec, status);
 }
 
 }  // namespace cgh

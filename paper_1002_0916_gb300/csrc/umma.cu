@@ -169,6 +169,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
         // below are executed by whole warps
         const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accum_bar, 0));
         umma::fence_after_sync();
+        pdl_trigger();  // only the epilogue is left
         if (!ok) set_status(g.status, DEV_TIMEOUT);
         if (MODE == 1 && ok && !abort_flag) {
             adjoint_epilogue<BN, SPLIT, S::ACC1>(tmem + ((uint32_t)(q * 32) << 16),

@@ -203,6 +203,7 @@ umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
     umma2::cluster_sync();
     umma::fence_after_sync();
     const uint32_t tmem = tmem_base;
+    pdl_wait();  // operands come from (and D may be read by) the kernel before
 
     if (warp == 0 && lane == 0) {
         // ------------------------------------------ producer (both CTAs)
@@ -282,6 +283,7 @@ umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
         const int row = m0 + q * 32 + lane;
         const bool ok = __all_sync(0xffffffffu, umma2::wait_cluster_bounded(&accum_bar, 0));
         umma::fence_after_sync();
+        pdl_trigger();  // only the epilogue is left
         if (!ok) set_status(g.status, DEV_TIMEOUT);
         if (MODE == 1 && ok && !abort_flag) {
             adjoint_epilogue<BNP, SPLIT, S::ACC1>(tmem + ((uint32_t)(q * 32) << 16), row,
@@ -368,8 +370,8 @@ static cudaError_t launch_pair_t(const GemmOperands &op, unsigned *status,
     GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status};
     dim3 grid(2 * ((op.N + BNP - 1) / BNP), (op.M + 2 * S::BM - 1) / (2 * S::BM));
     const uint32_t idesc = umma::idesc_f16(2 * S::BM, BNP, op.bf16);
-    kern<<<grid, 192, S::SMEM, s>>>(tA, tB, tA2, tB2, g, ea, idesc);
-    return cudaGetLastError();
+    return launch_dependent(kern, grid, dim3(192), S::SMEM, s, tA, tB, tA2, tB2, g, ea,
+                            idesc);
 }
 
 // The pair widths compiled in (columns of one 256-row pair tile).
