@@ -462,6 +462,11 @@ def run_ours(args):
     cg.cgh_kernel_timing(h, False)
     dom = max((k for k in kt_all if kt_all[k][1] > 0), key=lambda k: kt_all[k][0])
 
+    # the two pipe rates the ALU rooflines are derived from, measured on this
+    # device (outside the timed region)
+    pipe_rates = None
+    if dom in ("direct", "naive", "batch", "bwd_direct", "recur", "simt"):
+        pipe_rates = cg.cgh_debug_pipe_rates(h, stream=stream)
     props = torch.cuda.get_device_properties(dev)
     sampler = ClockSampler(f"GPU-{props.uuid}" if getattr(props, "uuid", None)
                            else str(local))
@@ -548,6 +553,15 @@ def run_ours(args):
                 "unit": "Gpp/s", "frac": achieved / peak,
                 "peak_source": f"derived: {sms} SMs x {NOMINAL_MAX_MHZ:.0f} MHz max SM "
                                f"clock x {per_clk:.2f} updates/clk/SM ({src})"}
+        if pipe_rates:
+            # the same recipe bound with the measured rates in place of the
+            # nominal 16 MUFU cosines and 128 FMAs per clock per SM
+            m, f = pipe_rates["mufu_cos_per_clk_per_sm"], pipe_rates["fma_per_clk_per_sm"]
+            per_clk_m = {"simt": f / 2.0, "recur": m, "bwd_direct": (f + 6.0 * m) / 20.0
+                         }.get(dom, (f + 6.0 * m) / 9.0)
+            roof["measured_pipe_rates"] = dict(pipe_rates)
+            roof["peak_from_measured_rates"] = sms * per_clk_m * NOMINAL_MAX_MHZ * 1e6 / 1e9
+            roof["frac_of_measured_rates"] = achieved / roof["peak_from_measured_rates"]
         if dom != "simt":
             mufu_per_pp = 2.0 if dom == "bwd_direct" else 1.0
             roof["frac_mufu_only"] = achieved / (

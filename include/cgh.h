@@ -377,6 +377,18 @@ cgh_status cgh_debug_gemm(cgh_handle h, const void *A, const void *B,
 cgh_status cgh_debug_stalled_wait(cgh_handle h, long long limit_cycles,
                                   void *stream);
 
+/* Diagnostic: the two SM pipe rates that bound this library's ALU kernels,
+ * measured on the handle's device by two short microbenchmarks (two CTAs of
+ * 1024 threads per SM, eight independent dependency chains per thread):
+ * *mufu_per_clk = hardware cosines (__cosf: one MUFU operation each) per SM
+ * clock, *fma_per_clk = FP32 multiply-adds per SM clock issued as packed
+ * fma.rn.f32x2.  Counted with the SMs' own cycle counters, so independent
+ * of the clock the GPU runs at.  Synchronises `stream`; uses the handle's
+ * host-call staging workspace.  Errors: CGH_ERR_INVALID_ARG (null
+ * pointer), CGH_ERR_NOMEM, CGH_ERR_CUDA. */
+cgh_status cgh_debug_pipe_rates(cgh_handle h, double *mufu_per_clk,
+                                double *fma_per_clk, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,7 @@ __all__ = [
     "cgh_debug_gemm", "CGHFunction", "default_handle", "KERNELS",
     "cgh_kernel_timing", "cgh_kernel_time", "cgh_tune_batch",
     "cgh_kernel_timing_mask", "cgh_set_gemm_tiles", "GEMM_TILES",
+    "cgh_debug_pipe_rates",
 ]
 
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
@@ -88,6 +89,9 @@ def _load():
     L.cgh_set_direct_schedule.argtypes = [vp, ci]
     L.cgh_set_gemm_tiles.argtypes = [vp, ci]
     L.cgh_set_gemm_tiles.restype = ci
+    L.cgh_debug_pipe_rates.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), vp]
+    L.cgh_debug_pipe_rates.restype = ci
     L.cgh_tune.argtypes = [vp, ci, ci, ci, ci, vp, ctypes.POINTER(_Tile)]
     L.cgh_tune_batch.argtypes = [vp, ctypes.POINTER(_Problem), ci, ci, vp,
                                  ctypes.POINTER(_Tile)]
@@ -348,6 +352,16 @@ def cgh_set_direct_schedule(h, schedule="auto"):
     stage) units, split tiles summed in a fixed order) or "auto"."""
     st = _L().cgh_set_direct_schedule(h, SCHEDULES[schedule])
     _check(h, st, "cgh_set_direct_schedule")
+
+
+def cgh_debug_pipe_rates(h, stream=None) -> dict:
+    """Measured MUFU cosines and packed FP32 FMAs per SM clock on the
+    handle's device (see include/cgh.h)."""
+    mufu, fma = ctypes.c_double(), ctypes.c_double()
+    st = _L().cgh_debug_pipe_rates(h, ctypes.byref(mufu), ctypes.byref(fma),
+                                   _stream_ptr(stream))
+    _check(h, st, "cgh_debug_pipe_rates")
+    return {"mufu_cos_per_clk_per_sm": mufu.value, "fma_per_clk_per_sm": fma.value}
 
 
 GEMM_TILES = {"auto": 0, "single": 1, "pairs": 2}
