@@ -73,7 +73,9 @@ typedef enum {
      * a sum of an x part and a y part), as a tcgen05 tensor-core GEMM with
      * FP32 accumulation.  Operands in BF16 / FP16 (single pass, relative RMS
      * error about 1e-2 / 1e-3) or split hi+lo FP16 (three products,
-     * relative RMS error <= 1e-4). */
+     * relative RMS error <= 1e-4).  Tensor memory accumulates at most
+     * 16,384 values of k (8,192 points) per launch; larger N runs as
+     * consecutive launches whose partial products are added in FP32. */
     CGH_SEP_BF16 = 1,
     CGH_SEP_FP16 = 2,
     CGH_SEP_FP16X3 = 3,

@@ -572,6 +572,7 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
     cudaError_t e = pairs ? prepare_umma_grouped_pair() : prepare_umma_grouped();
     if (e != cudaSuccess) return cuda_fail(e, "grouped GEMM set-up");
     std::vector<GroupProb> gps(prep.size());
+    std::vector<GemmOperands> ops(prep.size());
     std::vector<int> pidx;
     for (int i = 0, k = 0; i < count; ++i)
         if (probs[i].N) pidx.push_back(i), ++k;
@@ -601,6 +602,8 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
         op.lo_scale = 1.0f / LO_SCALE;
         op.D = probs[pidx[k]].out;
         op.ldd = sp.Nx;
+        op.tiles = gemm_tiles;
+        ops[k] = op;
         if (!encode_group_prob(&gps[k], op, b_box))
             return fail(CGH_ERR_CUDA, "problem %d: tensor map encoding failed", pidx[k]);
     }
@@ -609,8 +612,14 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
     for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int c) { return prep[a].Kp > prep[c].Kp; });
+    // a problem whose product is longer than one K chunk runs as its own
+    // chunked GEMM launches after the grouped kernel (same graph)
+    std::vector<int> long_k;
+    for (int k : order)
+        if (prep[k].Kp > GEMM_K_CHUNK) long_k.push_back(k);
     std::vector<uint2> items;
     for (int k : order)
+        if (prep[k].Kp <= GEMM_K_CHUNK)
         for (int mt = 0; mt < (prep[k].Ny + TM - 1) / TM; ++mt)
             for (int nt = 0; nt < (prep[k].Nx + BN - 1) / BN; ++nt)
                 items.push_back(make_uint2((unsigned)k, (unsigned)mt | ((unsigned)nt << 16)));
@@ -662,8 +671,13 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
             d_prep);
         r = cudaGetLastError();
         if (r != cudaSuccess) return r;
-        return pairs ? launch_umma_grouped_pair(d_gp, d_items, nitems, d_status, sm_count, q)
-                     : launch_umma_grouped(d_gp, d_items, nitems, d_status, sm_count, q);
+        r = pairs ? launch_umma_grouped_pair(d_gp, d_items, nitems, d_status, sm_count, q)
+                  : launch_umma_grouped(d_gp, d_items, nitems, d_status, sm_count, q);
+        for (size_t i = 0; i < long_k.size() && r == cudaSuccess; ++i)
+            r = launch_umma_gemm(ops[long_k[i]], d_status, q);
+        return r;
     };
-    return run_batch_graph(key, meta_b, np ? 3 : 0, fill, enqueue, s, CGH_K_BATCH_SEP);
+    int nkernels = np ? 3 : 0;
+    for (int k : long_k) nkernels += gemm_k_chunks(prep[k].Kp);
+    return run_batch_graph(key, meta_b, nkernels, fill, enqueue, s, CGH_K_BATCH_SEP);
 }

@@ -224,8 +224,19 @@ struct GemmOperands {
     float *D;
     long long ldd;
     int tiles = CGH_GEMM_AUTO;  // a cgh_gemm_tiles value
+    int accumulate = 0;         // 1: D += product instead of D = product
 };
 bool gemm_operands_ok(const GemmOperands &op);
+// Longest K one launch accumulates in tensor memory.  The tensor cores' FP32
+// accumulation drops the low bits of every add; over a long run of
+// same-sign terms (points whose phases agree at a pixel) that bias grows
+// in proportion to K: measured 1.3e-4 relative (split FP16, 100,000
+// coincident points) for runs of 32,768.  Products of larger K therefore
+// run as consecutive launches of at most this many values of k, each
+// adding its partial product into D in FP32 with round to nearest: about
+// 6e-5 at worst.
+constexpr int GEMM_K_CHUNK = 16384;
+inline int gemm_k_chunks(int K) { return (K + GEMM_K_CHUNK - 1) / GEMM_K_CHUNK; }
 // umma2.cu: the same product on CTA pairs (256-row tiles over two SMs);
 // bnp = columns of a pair tile (one of the compiled widths)
 int pick_pair_n(int M, int N, int sms);

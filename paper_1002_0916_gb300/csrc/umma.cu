@@ -199,19 +199,7 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
 #pragma unroll
                     for (int i = 0; i < CH; ++i) v[i] = __uint_as_float(r[i]);
                 }
-                if (row < g.M) {
-                    const int col = n0 + c;
-                    if (vec && col + CH <= g.N) {
-#pragma unroll
-                        for (int i = 0; i < CH; i += 4)
-                            *reinterpret_cast<float4 *>(drow + col + i) =
-                                make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < CH; ++i)
-                            if (col + i < g.N) drow[col + i] = v[i];
-                    }
-                }
+                if (row < g.M) epilogue_store_row<CH>(drow, n0 + c, v, g, vec);
             }
         }
     }
@@ -289,7 +277,7 @@ static cudaError_t launch_gemm_t(const GemmOperands &op, const AdjEpiArgs &ea,
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status};
+    GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status, op.accumulate};
     dim3 grid((op.N + BN - 1) / BN, (op.M + S::BM - 1) / S::BM);
     const uint32_t idesc = umma::idesc_f16(S::BM, BN, op.bf16);
     return launch_dependent(kern, grid, dim3(192), S::SMEM, s, tA, tB, tA2, tB2, g,
@@ -337,6 +325,24 @@ static int pick_tile_n(int M, int N, int sms) {
 cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
                              cudaStream_t s) {
     if (!gemm_operands_ok(op)) return cudaErrorInvalidValue;
+    if (op.K > GEMM_K_CHUNK) {
+        // consecutive launches over K chunks, the later ones adding into D
+        for (int k0 = 0; k0 < op.K; k0 += GEMM_K_CHUNK) {
+            GemmOperands c = op;
+            const size_t off = (size_t)k0 * 2;  // bytes of 16-bit elements
+            c.K = op.K - k0 < GEMM_K_CHUNK ? op.K - k0 : GEMM_K_CHUNK;
+            c.A_hi = (const char *)op.A_hi + off;
+            c.B_hi = (const char *)op.B_hi + off;
+            if (op.split) {
+                c.A_lo = (const char *)op.A_lo + off;
+                c.B_lo = (const char *)op.B_lo + off;
+            }
+            c.accumulate = op.accumulate || k0 > 0;
+            cudaError_t e = launch_umma_gemm(c, status, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     AdjEpiArgs ea{};
     const int sms = sm_count_of_current_device();
     // CTA pairs halve each SM's operand bytes per multiply-add; measured on

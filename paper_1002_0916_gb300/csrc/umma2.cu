@@ -313,19 +313,7 @@ umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
 #pragma unroll
                     for (int i = 0; i < CH; ++i) v[i] = __uint_as_float(r[i]);
                 }
-                if (row < g.M) {
-                    const int col = np0 + c;
-                    if (vec && col + CH <= g.N) {
-#pragma unroll
-                        for (int i = 0; i < CH; i += 4)
-                            *reinterpret_cast<float4 *>(drow + col + i) =
-                                make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < CH; ++i)
-                            if (col + i < g.N) drow[col + i] = v[i];
-                    }
-                }
+                if (row < g.M) epilogue_store_row<CH>(drow, np0 + c, v, g, vec);
             }
         }
     }
@@ -367,7 +355,7 @@ static cudaError_t launch_pair_t(const GemmOperands &op, unsigned *status,
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status};
+    GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status, op.accumulate};
     dim3 grid(2 * ((op.N + BNP - 1) / BNP), (op.M + 2 * S::BM - 1) / (2 * S::BM));
     const uint32_t idesc = umma::idesc_f16(2 * S::BM, BNP, op.bf16);
     return launch_dependent(kern, grid, dim3(192), S::SMEM, s, tA, tB, tA2, tB2, g, ea,

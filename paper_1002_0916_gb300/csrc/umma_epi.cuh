@@ -14,7 +14,34 @@ struct GemmArgs {
     long long ldd;
     float lo_scale;
     unsigned *status;
+    int accumulate;  // 0: D = product; 1: D += product (a later K chunk)
 };
+
+// Store CH consecutive FP32 values of one output row (row < M checked by the
+// caller), clipped to N columns; with g.accumulate the row's current values
+// are added first (FP32, round to nearest).
+template <int CH>
+__device__ __forceinline__ void epilogue_store_row(float *drow, int col, float (&v)[CH],
+                                                   const GemmArgs &g, bool vec) {
+    if (vec && col + CH <= g.N) {
+#pragma unroll
+        for (int i = 0; i < CH; i += 4) {
+            float4 o = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            if (g.accumulate) {
+                const float4 d = *reinterpret_cast<const float4 *>(drow + col + i);
+                o.x += d.x;
+                o.y += d.y;
+                o.z += d.z;
+                o.w += d.w;
+            }
+            *reinterpret_cast<float4 *>(drow + col + i) = o;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < CH; ++i)
+            if (col + i < g.N) drow[col + i] = g.accumulate ? drow[col + i] + v[i] : v[i];
+    }
+}
 
 // Fused adjoint epilogue (MODE 1).  The GEMM rows are k = 2j + c (c = 0:
 // cos row, 1: sin row of point j) and its columns are pixel coordinates u

@@ -1,0 +1,172 @@
+"""Edge cases of the point cloud for every forward method, against the FP64
+oracle through the C ABI: the maximum point count (N = 2^24) and one past
+it, and degenerate clouds (coincident points, points exactly on pixels,
+near-zero phase from a very distant point, zero and negative amplitudes,
+points far outside the frame).
+Bounds: FP32 paths max |I - I_ref| <= 1e-4 sum|A_j|; split FP16 relative
+RMS <= 1e-4 (or, where I_ref is near zero, max error <= 1e-4 sum|A_j|)."""
+import numpy as np
+import pytest
+
+from gpu_util import max_abs, rel_rms, sum_abs_A, to_dev
+from workloads import Cloud, make_cloud
+
+pytestmark = pytest.mark.gpu
+
+FP32 = ["direct", "naive", "recur", "sep_fp32"]
+METHODS = FP32 + ["sep_fp16x3"]
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_1002_0916_gb300 as cg
+    return cg
+
+
+@pytest.fixture(scope="module")
+def h(cg):
+    handle = cg.cgh_create(0)
+    yield handle
+    cg.cgh_destroy(handle)
+
+
+def _fwd(cg, h, c, method):
+    import torch
+    pts, A, z = to_dev(c)
+    I = cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, method=method, handle=h)
+    torch.cuda.synchronize()
+    assert cg.cgh_last_device_status(h) == cg.CGH_OK
+    return I.cpu().numpy()
+
+
+def _check(c, got, ref, method):
+    tol = 1e-4 * sum_abs_A(c)
+    assert np.all(np.isfinite(got))
+    if method in FP32:
+        assert max_abs(got, ref) <= tol, method
+    else:
+        assert rel_rms(got, ref) <= 1e-4 or max_abs(got, ref) <= tol, method
+
+
+def _degenerate_cloud(Nx, Ny):
+    rng = np.random.default_rng(2024)
+    xy, A, z = [], [], []
+    for _ in range(16):          # coincident points on a pixel
+        xy.append((10.0, 7.0)); A.append(0.25); z.append(0.4)
+    for k in range(8):           # points exactly on other pixels
+        xy.append((float(3 * k), float(2 * k))); A.append(1.0); z.append(0.3 + 0.05 * k)
+    xy.append((20.0, 20.0)); A.append(0.7); z.append(5.0e4)   # phase ~ 0: a plane wave
+    xy.append((5.0, 5.0)); A.append(0.0); z.append(0.5)       # zero amplitude
+    xy.append((30.5, 11.25)); A.append(-0.8); z.append(0.6)   # negative amplitude
+    xy.append((-1.0e4, 3.0)); A.append(0.5); z.append(0.9)    # far outside the frame
+    xy.append((Nx + 2.0e3, -7.5e3)); A.append(0.3); z.append(1.1)
+    for _ in range(9):           # ordinary points
+        xy.append((rng.uniform(0, Nx), rng.uniform(0, Ny))); A.append(rng.uniform())
+        z.append(rng.uniform(0.2, 1.0))
+    return Cloud(xy=np.array(xy, np.float32), A=np.array(A, np.float32),
+                 z=np.array(z, np.float32), lam=532e-9, p=8e-6, Nx=Nx, Ny=Ny,
+                 name="degenerate")
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_degenerate_cloud(cg, h, oracle_mod, method):
+    c = _degenerate_cloud(131, 67)
+    _check(c, _fwd(cg, h, c, method), oracle_mod.forward(c), method)
+
+
+@pytest.mark.parametrize("method", ["direct", "sep_fp16x3"])
+def test_all_points_coincident(cg, h, oracle_mod, method):
+    """N copies of one point: the hologram is N times one Fresnel zone
+    pattern, which the oracle's pins fix; any per-point indexing error shows."""
+    N = 1000
+    c = Cloud(xy=np.tile(np.array([[40.0, 25.0]], np.float32), (N, 1)),
+              A=np.full(N, 0.5, np.float32), z=np.full(N, 0.35, np.float32),
+              lam=633e-9, p=6.4e-6, Nx=97, Ny=53)
+    _check(c, _fwd(cg, h, c, method), oracle_mod.forward(c), method)
+
+
+@pytest.mark.parametrize("method", ["direct", "recur", "naive", "sep_fp16x3"])
+def test_maximum_point_count(cg, h, oracle_mod, method):
+    """N = 2^24 points (the largest N the ABI accepts) on a small frame:
+    point padding, the split schedule and 64-bit table offsets at their
+    limit."""
+    N = 1 << 24
+    c = make_cloud(24, N, 8, 8, integer=False, zlo=0.5, zhi=1.5, lam=633e-9,
+                   p=6.4e-6)
+    _check(c, _fwd(cg, h, c, method), oracle_mod.forward(c), method)
+
+
+def test_point_count_above_the_limit_is_rejected(cg, h):
+    import ctypes
+
+    import torch
+    N = (1 << 24) + 1
+    pts = torch.zeros((N, 2), device="cuda")
+    A = torch.zeros(N, device="cuda")
+    z = torch.ones(N, device="cuda")
+    out = torch.full((4, 4), 3.0, device="cuda")
+    p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    st = cg.lib.cgh_forward(h, p(pts), p(A), p(z), N, 532e-9, 8e-6, 4, 4, p(out), 0,
+                            None)
+    assert st == cg.CGH_ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert torch.all(out == 3.0)
+
+
+@pytest.mark.parametrize("tiles", ["auto", "single"])
+def test_coherent_sum_longer_than_one_k_chunk(cg, oracle_mod, tiles):
+    """100,000 coincident points (every term of a pixel's sum has the same
+    phase): the split-FP16 product runs in several K chunks whose partial
+    products are added in FP32 with round to nearest, so the tensor cores'
+    accumulation never runs over more than 16,384 values of k."""
+    import torch
+    N = 100000
+    c = Cloud(xy=np.tile(np.array([[150.0, 60.0]], np.float32), (N, 1)),
+              A=np.full(N, 0.5, np.float32), z=np.full(N, 0.8, np.float32),
+              lam=633e-9, p=6.4e-6, Nx=300, Ny=200)
+    hh = cg.cgh_create(0)
+    try:
+        cg.cgh_set_gemm_tiles(hh, tiles)
+        n0 = cg.cgh_launch_count(hh)
+        got = _fwd(cg, hh, c, "sep_fp16x3")
+        # prologue, tables and ceil(200,000 / 16,384) = 13 GEMM chunks
+        assert cg.cgh_launch_count(hh) - n0 == 2 + 13
+    finally:
+        cg.cgh_destroy(hh)
+    assert rel_rms(got, oracle_mod.forward(c)) <= 1e-4
+
+
+def test_batch_with_a_problem_longer_than_one_k_chunk(cg, oracle_mod):
+    """A separable batch mixing ordinary problems with one of 20,000 points
+    (K = 40,000 > 16,384): the long one runs as chunked launches in the same
+    graph; every hologram within the split-FP16 bound."""
+    import torch
+    clouds = [make_cloud(5, 300, 200, 150, integer=True, zlo=0.3, zhi=1.0,
+                         lam=532e-9, p=8e-6),
+              Cloud(xy=np.tile(np.array([[90.0, 40.0]], np.float32), (20000, 1)),
+                    A=np.full(20000, 0.25, np.float32),
+                    z=np.full(20000, 0.6, np.float32), lam=633e-9, p=8e-6,
+                    Nx=180, Ny=130),
+              make_cloud(6, 50, 77, 64, integer=False, zlo=0.3, zhi=1.0,
+                         lam=473e-9, p=8e-6)]
+    hh = cg.cgh_create(0)
+    try:
+        probs = []
+        for cl in clouds:
+            pts, A, z = to_dev(cl)
+            probs.append(dict(points=pts, A=A, z=z, lam=cl.lam, p=cl.p, Nx=cl.Nx,
+                              Ny=cl.Ny, out=torch.full((cl.Ny, cl.Nx), float("nan"),
+                                                       device="cuda")))
+        for _ in range(2):  # the first call builds the graph, the second replays it
+            cg.cgh_batch(probs, method="sep_fp16x3", handle=hh)
+            torch.cuda.synchronize()
+            assert cg.cgh_last_device_status(hh) == cg.CGH_OK
+            for cl, pr in zip(clouds, probs):
+                assert rel_rms(pr["out"].cpu().numpy(), oracle_mod.forward(cl)) <= 1e-4
+            for pr in probs:
+                pr["out"].fill_(float("nan"))
+    finally:
+        cg.cgh_destroy(hh)
