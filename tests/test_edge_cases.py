@@ -170,3 +170,100 @@ def test_batch_with_a_problem_longer_than_one_k_chunk(cg, oracle_mod):
                 pr["out"].fill_(float("nan"))
     finally:
         cg.cgh_destroy(hh)
+
+
+@pytest.mark.parametrize("method", ["recur", "sep_fp32", "sep_fp16x3", "sep_bf16"])
+@pytest.mark.parametrize("Nx,Ny", [(32768, 3), (1, 4099), (5, 1), (1, 1)])
+def test_extreme_frame_shapes(cg, h, oracle_mod, method, Nx, Ny):
+    """The widest and the tallest frames the ABI accepts next to one-pixel
+    ones, for the methods the direct tests do not cover."""
+    c = make_cloud(11, 40, Nx, Ny, integer=False, zlo=0.5, zhi=1.5, lam=473e-9,
+                   p=8e-6)
+    got = _fwd(cg, h, c, method)
+    ref = oracle_mod.forward(c)
+    if method == "sep_bf16":
+        assert rel_rms(got, ref) <= 1e-2 or max_abs(got, ref) <= 1e-2 * sum_abs_A(c)
+    else:
+        _check(c, got, ref, method)
+
+
+def _bwd(cg, h, c, G, method):
+    import torch
+    pts, A, z = to_dev(c)
+    Gd = torch.from_numpy(np.ascontiguousarray(G, dtype=np.float32)).cuda()
+    gp, gA, gz = cg.cgh_backward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, Gd,
+                                 method=method, handle=h)
+    torch.cuda.synchronize()
+    assert cg.cgh_last_device_status(h) == cg.CGH_OK
+    return gp.cpu().numpy(), gA.cpu().numpy(), gz.cpu().numpy()
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("method", ["direct", "sep_fp16x3"])
+def test_adjoint_many_points(cg, h, oracle_mod, method):
+    """50,000 points on a small frame: many GEMM rows (2N) and many
+    point-owned CTAs; oracle gradient on sampled points, bound 1e-3 per
+    parameter group."""
+    from workloads import grad_field
+    c = make_cloud(50, 50000, 64, 48, integer=False, zlo=0.3, zhi=1.2, lam=532e-9,
+                   p=8e-6)
+    G = grad_field(51, c.Nx, c.Ny)
+    gp, gA, gz = _bwd(cg, h, c, G, method)
+    sel = np.sort(np.random.default_rng(52).choice(c.N, 24, replace=False))
+    rp, rA, rz = oracle_mod.grad(c, G.astype(np.float64), pts=sel)
+    for got, ref in ((gA[sel], rA), (gp[sel, 0], rp[:, 0]), (gp[sel, 1], rp[:, 1]),
+                     (gz[sel], rz)):
+        assert _rel(got, ref) <= 1e-3
+
+
+@pytest.mark.parametrize("method", ["direct", "sep_fp16x3"])
+def test_adjoint_degenerate_cloud_and_zero_gradient(cg, h, oracle_mod, method):
+    """Coincident points, points on pixels, zero and negative amplitudes and
+    points far outside the frame; and dL/dI = 0, whose gradient is exactly
+    zero."""
+    c = _degenerate_cloud(131, 67)
+    from workloads import grad_field
+    G = grad_field(53, c.Nx, c.Ny)
+    gp, gA, gz = _bwd(cg, h, c, G, method)
+    rp, rA, rz = oracle_mod.grad(c, G.astype(np.float64))
+    for got, ref in ((gA, rA), (gp[:, 0], rp[:, 0]), (gp[:, 1], rp[:, 1]), (gz, rz)):
+        assert _rel(got, ref) <= 1e-3
+    zp, zA, zz = _bwd(cg, h, c, np.zeros_like(G), method)
+    assert not np.any(zp) and not np.any(zA) and not np.any(zz)
+
+
+def test_batch_of_degenerate_and_empty_problems(cg, oracle_mod):
+    """A batch holding a degenerate cloud, an empty cloud and a one-pixel
+    frame, by both methods."""
+    import torch
+    clouds = [_degenerate_cloud(131, 67),
+              Cloud(xy=np.zeros((0, 2), np.float32), A=np.zeros(0, np.float32),
+                    z=np.zeros(0, np.float32), lam=532e-9, p=8e-6, Nx=40, Ny=30),
+              make_cloud(9, 17, 1, 1, integer=False, zlo=0.4, zhi=0.9, lam=633e-9,
+                         p=8e-6)]
+    hh = cg.cgh_create(0)
+    try:
+        for method in ("direct", "sep_fp16x3"):
+            probs = []
+            for cl in clouds:
+                pts, A, z = to_dev(cl)
+                probs.append(dict(points=pts, A=A, z=z, lam=cl.lam, p=cl.p, Nx=cl.Nx,
+                                  Ny=cl.Ny, out=torch.full((cl.Ny, cl.Nx), float("nan"),
+                                                           device="cuda")))
+            cg.cgh_batch(probs, method=method, handle=hh)
+            torch.cuda.synchronize()
+            assert cg.cgh_last_device_status(hh) == cg.CGH_OK
+            for cl, pr in zip(clouds, probs):
+                got = pr["out"].cpu().numpy()
+                if cl.N == 0:
+                    assert np.count_nonzero(got) == 0
+                    continue
+                _check(cl, got, oracle_mod.forward(cl),
+                       "direct" if method == "direct" else "sep_fp16x3")
+    finally:
+        cg.cgh_destroy(hh)
