@@ -74,8 +74,9 @@ typedef enum {
      * FP32 accumulation.  Operands in BF16 / FP16 (single pass, relative RMS
      * error about 1e-2 / 1e-3) or split hi+lo FP16 (three products,
      * relative RMS error <= 1e-4).  Tensor memory accumulates at most
-     * 16,384 values of k (8,192 points) per launch; larger N runs as
-     * consecutive launches whose partial products are added in FP32. */
+     * 16,384 values of k (8,192 points; single pass: 131,072) per launch;
+     * larger N runs as consecutive launches whose partial products are
+     * added in FP32. */
     CGH_SEP_BF16 = 1,
     CGH_SEP_FP16 = 2,
     CGH_SEP_FP16X3 = 3,

@@ -616,10 +616,10 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
     // chunked GEMM launches after the grouped kernel (same graph)
     std::vector<int> long_k;
     for (int k : order)
-        if (prep[k].Kp > GEMM_K_CHUNK) long_k.push_back(k);
+        if (prep[k].Kp > gemm_k_chunk(true)) long_k.push_back(k);
     std::vector<uint2> items;
     for (int k : order)
-        if (prep[k].Kp <= GEMM_K_CHUNK)
+        if (prep[k].Kp <= gemm_k_chunk(true))
         for (int mt = 0; mt < (prep[k].Ny + TM - 1) / TM; ++mt)
             for (int nt = 0; nt < (prep[k].Nx + BN - 1) / BN; ++nt)
                 items.push_back(make_uint2((unsigned)k, (unsigned)mt | ((unsigned)nt << 16)));
@@ -678,6 +678,6 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
         return r;
     };
     int nkernels = np ? 3 : 0;
-    for (int k : long_k) nkernels += gemm_k_chunks(prep[k].Kp);
+    for (int k : long_k) nkernels += gemm_k_chunks(prep[k].Kp, true);
     return run_batch_graph(key, meta_b, nkernels, fill, enqueue, s, CGH_K_BATCH_SEP);
 }

@@ -230,13 +230,18 @@ bool gemm_operands_ok(const GemmOperands &op);
 // Longest K one launch accumulates in tensor memory.  The tensor cores' FP32
 // accumulation drops the low bits of every add; over a long run of
 // same-sign terms (points whose phases agree at a pixel) that bias grows
-// in proportion to K: measured 1.3e-4 relative (split FP16, 100,000
-// coincident points) for runs of 32,768.  Products of larger K therefore
-// run as consecutive launches of at most this many values of k, each
-// adding its partial product into D in FP32 with round to nearest: about
-// 6e-5 at worst.
+// in proportion to K: measured 1.3e-4 relative (100,000 coincident
+// points) for runs of 32,768, about 4e-9 per value of k.  Products of
+// larger K therefore run as consecutive launches of at most this many
+// values of k, each adding its partial product into D in FP32 with round
+// to nearest: 16,384 for split FP16 (bound 1e-4: about 6e-5 at worst),
+// 131,072 for the single-pass forms (bound 1e-2: about 5e-4 at worst).
 constexpr int GEMM_K_CHUNK = 16384;
-inline int gemm_k_chunks(int K) { return (K + GEMM_K_CHUNK - 1) / GEMM_K_CHUNK; }
+constexpr int GEMM_K_CHUNK_SINGLE = 131072;
+inline int gemm_k_chunk(bool split) { return split ? GEMM_K_CHUNK : GEMM_K_CHUNK_SINGLE; }
+inline int gemm_k_chunks(int K, bool split) {
+    return (K + gemm_k_chunk(split) - 1) / gemm_k_chunk(split);
+}
 // umma2.cu: the same product on CTA pairs (256-row tiles over two SMs);
 // bnp = columns of a pair tile (one of the compiled widths)
 int pick_pair_n(int M, int N, int sms);

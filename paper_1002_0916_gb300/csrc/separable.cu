@@ -136,7 +136,7 @@ cgh_status cgh_ctx::forward_separable(const float *points, const float *A,
         TimedLaunch tl(this, CGH_K_GEMM, s);
         cudaError_t e = launch_umma_gemm(op, d_status, s);
         if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
-        launches += gemm_k_chunks(Kp) - 1;  // K chunks beyond the first
+        launches += gemm_k_chunks(Kp, split) - 1;  // K chunks beyond the first
         tl.done();
     }
     return CGH_OK;

@@ -325,12 +325,13 @@ static int pick_tile_n(int M, int N, int sms) {
 cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
                              cudaStream_t s) {
     if (!gemm_operands_ok(op)) return cudaErrorInvalidValue;
-    if (op.K > GEMM_K_CHUNK) {
+    const int chunk = gemm_k_chunk(op.split);
+    if (op.K > chunk) {
         // consecutive launches over K chunks, the later ones adding into D
-        for (int k0 = 0; k0 < op.K; k0 += GEMM_K_CHUNK) {
+        for (int k0 = 0; k0 < op.K; k0 += chunk) {
             GemmOperands c = op;
             const size_t off = (size_t)k0 * 2;  // bytes of 16-bit elements
-            c.K = op.K - k0 < GEMM_K_CHUNK ? op.K - k0 : GEMM_K_CHUNK;
+            c.K = op.K - k0 < chunk ? op.K - k0 : chunk;
             c.A_hi = (const char *)op.A_hi + off;
             c.B_hi = (const char *)op.B_hi + off;
             if (op.split) {
