@@ -635,6 +635,12 @@ def run_ours(args):
                "l2": "flushed: 256 MiB device write between timed steps",
                "parallelism": ("replicas (each rank its own copy of the workload)"
                                if world > 1 else "single GPU")}
+        if args.workload in ("paper", "large", "adjoint"):
+            cfg["direct_tile"] = dict(zip(
+                ("tile_x", "tile_y", "vec_x", "vec_y", "points_per_stage",
+                 "poly_pixels", "point_groups", "packed"),
+                cg.cgh_direct_tile_for(h, c.N, c.Nx, c.Ny)))
+            cfg["gemm_tiles"] = "auto (CTA pairs above 128 rows)"
         if args.workload == "table1":
             cfg["workload"] = ("1920x1024 pixels, N = 512, 1024, ..., 3584 points (the "
                                "paper's Table 1 sweep), otherwise the 1920x1024x1024 "

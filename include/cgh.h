@@ -289,6 +289,13 @@ cgh_status cgh_set_gemm_tiles(cgh_handle h, int tiles);
 int cgh_direct_tile_count(void);
 cgh_status cgh_direct_tile_get(int i, cgh_direct_tile *out);
 
+/* The tile shape this handle's CGH_DIRECT_FP32 calls use for N points on
+ * an Nx x Ny frame (the forced shape, else the tuned one for that size
+ * bucket, else the built-in heuristic's).  Errors: CGH_ERR_INVALID_ARG for
+ * a null pointer or sizes cgh_forward would reject (N = 0 included). */
+cgh_status cgh_direct_tile_for(cgh_handle h, int N, int Nx, int Ny,
+                               cgh_direct_tile *out);
+
 /* Force a tile shape for CGH_DIRECT_FP32 (NULL: back to automatic choice).
  * Errors: CGH_ERR_UNSUPPORTED if the shape is not compiled in. */
 cgh_status cgh_set_direct_tile(cgh_handle h, const cgh_direct_tile *tile);

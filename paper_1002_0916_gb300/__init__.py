@@ -31,7 +31,7 @@ __all__ = [
     "cgh_debug_gemm", "CGHFunction", "default_handle", "KERNELS",
     "cgh_kernel_timing", "cgh_kernel_time", "cgh_tune_batch",
     "cgh_kernel_timing_mask", "cgh_set_gemm_tiles", "GEMM_TILES",
-    "cgh_debug_pipe_rates",
+    "cgh_debug_pipe_rates", "cgh_direct_tile_for",
 ]
 
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
@@ -87,6 +87,8 @@ def _load():
     L.cgh_direct_tile_get.argtypes = [ci, ctypes.POINTER(_Tile)]
     L.cgh_set_direct_tile.argtypes = [vp, ctypes.POINTER(_Tile)]
     L.cgh_set_direct_schedule.argtypes = [vp, ci]
+    L.cgh_direct_tile_for.argtypes = [vp, ci, ci, ci, ctypes.POINTER(_Tile)]
+    L.cgh_direct_tile_for.restype = ci
     L.cgh_set_gemm_tiles.argtypes = [vp, ci]
     L.cgh_set_gemm_tiles.restype = ci
     L.cgh_debug_pipe_rates.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
@@ -332,6 +334,16 @@ def cgh_direct_tiles():
         out.append((t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage,
                     t.poly_pixels, t.point_groups, t.packed))
     return out
+
+
+def cgh_direct_tile_for(h, N: int, Nx: int, Ny: int):
+    """The direct tile shape (as in cgh_direct_tiles()) the handle uses for
+    this problem size."""
+    t = _Tile()
+    st = _L().cgh_direct_tile_for(h, int(N), int(Nx), int(Ny), ctypes.byref(t))
+    _check(h, st, "cgh_direct_tile_for")
+    return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage,
+            t.poly_pixels, t.point_groups, t.packed)
 
 
 def cgh_set_direct_tile(h, tile=None):

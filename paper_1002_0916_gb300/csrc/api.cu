@@ -529,6 +529,14 @@ const char *cgh_last_error(cgh_handle h) { return h ? h->err : ""; }
 
 int cgh_direct_tile_count(void) { return direct_tile_count(); }
 
+cgh_status cgh_direct_tile_for(cgh_handle h, int N, int Nx, int Ny,
+                               cgh_direct_tile *out) {
+    if (!h || !out || N < 1 || N > CGH_MAX_POINTS || Nx < 1 || Ny < 1 ||
+        Nx > CGH_MAX_SIDE || Ny > CGH_MAX_SIDE)
+        return CGH_ERR_INVALID_ARG;
+    return cgh_direct_tile_get(h->pick_direct_tile(N, Nx, Ny), out);
+}
+
 cgh_status cgh_direct_tile_get(int i, cgh_direct_tile *out) {
     if (!out || i < 0 || i >= direct_tile_count()) return CGH_ERR_INVALID_ARG;
     DirectTile t = direct_tile_get(i);

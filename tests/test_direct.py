@@ -240,3 +240,23 @@ def test_schedule_argument_errors(cg, h):
     assert cg.lib.cgh_set_direct_schedule(h, 7) == cg.CGH_ERR_INVALID_ARG
     assert cg.lib.cgh_set_direct_schedule(None, 0) == cg.CGH_ERR_INVALID_ARG
     cg.cgh_set_direct_schedule(h, "auto")
+
+
+def test_direct_tile_query(cg, h):
+    """cgh_direct_tile_for reports the shape the handle's direct calls use: a
+    compiled shape, the forced one while forced, and the tuned one after
+    tuning that size."""
+    tiles = cg.cgh_direct_tiles()
+    auto = cg.cgh_direct_tile_for(h, 1024, 1920, 1024)
+    assert auto in tiles
+    forced = tiles[0] if tiles[0] != auto else tiles[1]
+    try:
+        cg.cgh_set_direct_tile(h, forced)
+        assert cg.cgh_direct_tile_for(h, 1024, 1920, 1024) == forced
+    finally:
+        cg.cgh_set_direct_tile(h, None)
+    assert cg.cgh_direct_tile_for(h, 1024, 1920, 1024) == auto
+    tuned = cg.cgh_tune(h, 200, 96, 64)
+    assert cg.cgh_direct_tile_for(h, 200, 96, 64) == tuned
+    with pytest.raises(cg.CGHError):
+        cg.cgh_direct_tile_for(h, 0, 8, 8)
