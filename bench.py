@@ -14,7 +14,7 @@ step, summed over ranks, / step time; the per-method times are in "methods".
 Multi-GPU (torchrun, one rank per GPU): every rank computes its own copy of
 the workload (replicas, weak scaling); no collective touches the data path.
 --impl reference times the FP64 CPU oracle on the host cores instead (the
-reference arm for this build: there is no reference GPU code).
+paper ships no code, so the oracle is the reference arm).
 """
 from __future__ import annotations
 

@@ -57,7 +57,7 @@ typedef enum {
     CGH_ERR_INVALID_ARG = 1,  /* rejected argument (host) or bad point (device) */
     CGH_ERR_CUDA = 2,         /* a CUDA call failed; cgh_last_error() has text   */
     CGH_ERR_NOMEM = 3,        /* workspace allocation failed                     */
-    CGH_ERR_UNSUPPORTED = 4,  /* valid request this build cannot serve           */
+    CGH_ERR_UNSUPPORTED = 4,  /* valid request this library cannot serve         */
     CGH_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up              */
 } cgh_status;
 
@@ -284,7 +284,7 @@ typedef enum {
  * value. */
 cgh_status cgh_set_gemm_tiles(cgh_handle h, int tiles);
 
-/* Number of direct-kernel tile shapes compiled into this build, and the
+/* Number of direct-kernel tile shapes compiled into this library, and the
  * i-th of them (0 <= i < count). */
 int cgh_direct_tile_count(void);
 cgh_status cgh_direct_tile_get(int i, cgh_direct_tile *out);
