@@ -325,6 +325,21 @@ void cgh_ctx::timer_reset() {
 }
 
 // ============================================================ the C ABI
+const char *method_range_name(bool host, int method) {
+    // one static string per (entry, method): NVTX copies nothing
+    static const char *const fwd[] = {"cgh_forward direct", "cgh_forward sep_bf16",
+                                      "cgh_forward sep_fp16", "cgh_forward sep_fp16x3",
+                                      "cgh_forward naive", "cgh_forward recur",
+                                      "cgh_forward sep_fp32"};
+    static const char *const hosts[] = {
+        "cgh_forward_host direct", "cgh_forward_host sep_bf16",
+        "cgh_forward_host sep_fp16", "cgh_forward_host sep_fp16x3",
+        "cgh_forward_host naive", "cgh_forward_host recur", "cgh_forward_host sep_fp32"};
+    const bool known = method >= 0 && method < (int)(sizeof(fwd) / sizeof(fwd[0]));
+    if (host) return known ? hosts[method] : "cgh_forward_host";
+    return known ? fwd[method] : "cgh_forward";
+}
+
 extern "C" {
 
 cgh_status cgh_create(cgh_handle *out, int device) {
@@ -388,6 +403,7 @@ cgh_status cgh_destroy(cgh_handle h) {
 cgh_status cgh_forward(cgh_handle h, const float *points, const float *A,
                        const float *z, int N, double lambda, double p, int Nx,
                        int Ny, float *out, int method, void *stream) {
+    NvtxRange range(method_range_name(false, method));
     if (!h) return CGH_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     h->err[0] = 0;
@@ -411,6 +427,7 @@ cgh_status cgh_forward_host(cgh_handle h, const float *points_host,
                             const float *A_host, const float *z_host, int N,
                             double lambda, double p, int Nx, int Ny,
                             float *out_host, int method, void *stream) {
+    NvtxRange range(method_range_name(true, method));
     if (!h) return CGH_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     h->err[0] = 0;

@@ -11,6 +11,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cgh.h"
 
 #define CGH_MAX_POINTS (1 << 24)
@@ -126,6 +128,17 @@ std::string size_bucket(int method, int N, int Nx, int Ny);
 // batch.cu: tuning-cache key of a batch geometry (sizes only)
 std::string batch_bucket(const cgh_problem *probs, int count);
 int default_direct_tile(int N, int Nx, int Ny, int sm_count);
+
+// An NVTX range named after a public entry point (and, for the forward
+// calls, the method), open for the life of the call: visible to ncu --nvtx
+// and other NVTX tools, close to free when no tool is attached.
+const char *method_range_name(bool host, int method);
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Brackets one kernel launch with events when the handle's timing is on,
 // and counts the launch.

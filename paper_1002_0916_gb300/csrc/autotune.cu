@@ -103,6 +103,7 @@ void cgh_ctx::load_tune_cache() {
 
 extern "C" cgh_status cgh_tune(cgh_handle h, int N, int Nx, int Ny, int method,
                                void *stream, cgh_direct_tile *chosen) {
+    NvtxRange range("cgh_tune");
     if (!h) return CGH_ERR_INVALID_ARG;
     if (method != CGH_DIRECT_FP32)
         return h->fail(CGH_ERR_UNSUPPORTED,

@@ -458,6 +458,7 @@ extern "C" cgh_status cgh_backward(cgh_handle h, const float *points,
                                    const float *grad_out, float *grad_points,
                                    float *grad_A, float *grad_z, int method,
                                    void *stream) {
+    NvtxRange range("cgh_backward");
     if (!h) return CGH_ERR_INVALID_ARG;
     int prev = 0;
     cudaGetDevice(&prev);

@@ -433,6 +433,7 @@ std::string batch_bucket(const cgh_problem *probs, int count) {
 
 extern "C" cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int count,
                                 int method, void *stream) {
+    NvtxRange range("cgh_batch");
     if (!h) return CGH_ERR_INVALID_ARG;
     int prev = 0;
     cudaGetDevice(&prev);
@@ -446,6 +447,7 @@ extern "C" cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int coun
 extern "C" cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs,
                                      int count, int method, void *stream,
                                      cgh_direct_tile *chosen) {
+    NvtxRange range("cgh_tune_batch");
     if (!h) return CGH_ERR_INVALID_ARG;
     if (method != CGH_DIRECT_FP32)
         return h->fail(CGH_ERR_UNSUPPORTED, "only the direct batch has tunable tiles");

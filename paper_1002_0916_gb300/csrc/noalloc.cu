@@ -69,6 +69,7 @@ extern "C" cgh_status cgh_forward_noalloc(const float *points, const float *A,
                                           const float *z, int N, double lambda,
                                           double p, int Nx, int Ny, float *out,
                                           void *stream) {
+    NvtxRange range("cgh_forward_noalloc");
     if (N < 0 || N > CGH_MAX_POINTS || Nx < 1 || Ny < 1 || Nx > CGH_MAX_SIDE ||
         Ny > CGH_MAX_SIDE || !finite_pos(lambda) || !finite_pos(p) || !out ||
         (N > 0 && (!points || !A || !z)))
