@@ -379,6 +379,7 @@ cgh_status cgh_create(cgh_handle *out, int device) {
         const int v = atoi(f);
         if (v >= CGH_GEMM_AUTO && v <= CGH_GEMM_PAIRS) h->gemm_tiles = v;
     }
+    if (const char *f = getenv("CGH_BWD_STAGED")) h->bwd_staged = atoi(f) != 0;
     if (const char *f = getenv("CGH_BWD_POLY")) {
         const int v = atoi(f);
         if (v == 0 || v == 4 || v == 6) h->bwd_poly = v;

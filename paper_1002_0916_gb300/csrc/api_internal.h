@@ -69,6 +69,9 @@ struct cgh_ctx {
     // polynomial (FMA-pipe) sin/cos columns of the direct adjoint's 16-column
     // strips: 0, 4 (default) or 6; CGH_BWD_POLY at cgh_create
     int bwd_poly = 4;
+    // direct adjoint: G staged through shared memory by TMA where its layout
+    // allows (1) or read row by row from global memory (0); CGH_BWD_STAGED
+    int bwd_staged = 1;
     // stage shape of the FP32 separable product (index into the compiled
     // shapes; 1 = 32 values of k x 2 stages, the fastest measured);
     // CGH_SIMT_STAGE at cgh_create

@@ -251,6 +251,21 @@ bool make_gemm_map(CUtensorMap *m, const void *base, long long inner, long long 
     return make_map(m, base, inner, rows, ld, box_rows, bf16);
 }
 
+bool make_f32_map(CUtensorMap *m, const void *base, long long inner, long long rows,
+                  long long ld, int box_inner, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 template <int BN, bool SPLIT, int STAGES, int MODE>
 static cudaError_t launch_gemm_t(const GemmOperands &op, const AdjEpiArgs &ea,
                                  unsigned *status, cudaStream_t s) {

@@ -149,6 +149,12 @@ struct alignas(64) GroupProb {
 
 // Fill gp (tensor maps and sizes) for the split GEMM `op`; false if a
 // tensor map cannot be encoded.
+// Tensor map of a rows x inner FP32 matrix (row stride `ld` elements), box =
+// box_inner x box_rows, no swizzle, zero fill out of bounds.  inner * 4 and
+// ld * 4 must be multiples of 16 bytes, base 16-byte aligned.
+bool make_f32_map(CUtensorMap *m, const void *base, long long inner, long long rows,
+                  long long ld, int box_inner, int box_rows);
+
 // b_box_rows: rows of B per TMA box (the tile's columns for one-CTA items,
 // half of them for CTA-pair items)
 bool encode_group_prob(GroupProb *gp, const GemmOperands &op, int b_box_rows);
