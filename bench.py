@@ -315,6 +315,9 @@ MAIN_KERNEL = {"direct": "direct", "naive": "naive", "recur": "recur",
                "sep_fp32": "simt", "sep_fp16x3": "gemm", "sep_fp16": "gemm",
                "sep_bf16": "gemm"}
 GEMM_PASSES = {"sep_fp16x3": 3.0, "sep_fp16": 1.0, "sep_bf16": 1.0}
+# methods whose kernels store the hologram tile by tile (into mapped host
+# memory in place when the output is a pinned host buffer)
+PROGRESSIVE = {"direct", "naive", "recur", "sep_fp32"}
 
 
 def build_legs(cg, h, which, methods, dev, stream):
@@ -595,25 +598,51 @@ def run_ours(args):
         hp, hA, hz = pin(c.xy), pin(c.A), pin(c.z)
         hout = {m: torch.empty((c.Ny, c.Nx), dtype=torch.float32).pin_memory()
                 for m in fwd_methods}
-        for m in fwd_methods:
-            cg.cgh_forward_host(hp, hA, hz, c.lam, c.p, c.Nx, c.Ny, out=hout[m],
-                                method=m, handle=h, stream=stream)
-        barrier()
         E = max(3, K // 2)
-        t0 = time.perf_counter()
-        for _ in range(E):
+
+        def sync_step():
+            # each call returns with its hologram in host memory
             for m in fwd_methods:
                 cg.cgh_forward_host(hp, hA, hz, c.lam, c.p, c.Nx, c.Ny, out=hout[m],
                                     method=m, handle=h, stream=stream)
-        e2e_s = (time.perf_counter() - t0) / E
-        if dist is not None:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * len(fwd_methods) * c.pp / e2e_s, "unit": UNIT,
+
+        # pipelined: the tensor-core holograms first, so that their copies to
+        # the host run while the tile-by-tile kernels (which write their
+        # holograms to host memory as they go) compute; one wait per step
+        order = sorted(fwd_methods, key=lambda m: m in PROGRESSIVE)
+
+        def async_step():
+            for m in order:
+                cg.cgh_forward_host_async(hp, hA, hz, c.lam, c.p, c.Nx, c.Ny,
+                                          out=hout[m], method=m, handle=h,
+                                          stream=stream)
+            cg.cgh_host_wait(h, stream)
+
+        def timed(fn):
+            fn()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(E):
+                fn()
+            s = (time.perf_counter() - t0) / E
+            if dist is not None:
+                t = torch.tensor([s], device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                s = float(t.item())
+            return s
+
+        sync_s = timed(sync_step)
+        e2e_s = timed(async_step)
+        npp = world * len(fwd_methods) * c.pp
+        e2e = {"value": npp / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": len(fwd_methods) * c.N * 16,
                "d2h_bytes_per_step": len(fwd_methods) * c.Nx * c.Ny * 4,
-               "ms_per_step": e2e_s * 1e3}
+               "ms_per_step": e2e_s * 1e3,
+               "calls": "cgh_forward_host_async per hologram (" + ", ".join(order)
+                        + "), then cgh_host_wait",
+               "synchronous": {"value": npp / sync_s, "ms_per_step": sync_s * 1e3,
+                               "calls": "cgh_forward_host per hologram ("
+                                        + ", ".join(fwd_methods) + ")"}}
 
     table1 = None
     if args.workload == "table1":

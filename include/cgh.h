@@ -133,6 +133,31 @@ cgh_status cgh_forward_host(cgh_handle h, const float *points_host,
                             double lambda, double p, int Nx, int Ny,
                             float *out_host, int method, void *stream);
 
+/* cgh_forward_host without the synchronisation, for pipelines that compute
+ * hologram after hologram into host memory (a display loop feeding a
+ * spatial light modulator, a server).  All four host buffers must be
+ * page-locked and mapped (as above); otherwise CGH_ERR_INVALID_ARG and
+ * nothing is launched.  Inputs are read in place.  The methods that store
+ * the hologram tile by tile write out_host in place on `stream`; the
+ * tensor-core methods compute into one of two device buffers of the handle
+ * (used in turn) and copy it to out_host on a copy stream of the handle, so
+ * that the copy runs while the next call's kernels do.  A call waits on the
+ * device (not the host) for the copy out of its buffer two calls earlier.
+ * The inputs must stay unchanged, and out_host unread, until
+ * cgh_host_wait returns.  Not inside stream capture
+ * (CGH_ERR_UNSUPPORTED).  Results are bit for bit those of
+ * cgh_forward_host.  Other errors as cgh_forward. */
+cgh_status cgh_forward_host_async(cgh_handle h, const float *points_host,
+                                  const float *A_host, const float *z_host,
+                                  int N, double lambda, double p, int Nx,
+                                  int Ny, float *out_host, int method,
+                                  void *stream);
+
+/* Blocks until `stream` and every copy of earlier cgh_forward_host_async
+ * calls of the handle have finished: their host outputs are then complete.
+ * CGH_ERR_CUDA if either failed. */
+cgh_status cgh_host_wait(cgh_handle h, void *stream);
+
 /* Adjoint of Eq. 1.  grad_out: device, Ny*Nx floats, dL/dI for some loss L.
  * Writes (device, N entries each; grad_points N x 2 interleaved):
  *   grad_A[j]          = sum_pix G cos(phi)
@@ -192,7 +217,7 @@ cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int count,
  *
  * Computes the same hologram as cgh_forward(..., CGH_DIRECT_FP32, ...) on
  * the calling thread's current device, using the same kernels, but takes
- * all scratch (point records, angle tables, status word) from one fixed
+ * all scratch (angle tables, amplitudes, status word) from one fixed
  * __device__ array of CGH_NOALLOC_SCRATCH_BYTES.  It calls no cudaMalloc,
  * cudaFree or other allocating routine.  points, A, z, out: device memory
  * owned by the caller, layouts as cgh_forward; stream: cudaStream_t or NULL.
@@ -208,7 +233,7 @@ cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int count,
  *
  * Returns CGH_OK; CGH_ERR_INVALID_ARG for the argument errors cgh_forward
  * rejects; CGH_ERR_UNSUPPORTED when the frame needs more scratch than the
- * array holds (about (Nx + Ny) * N * 4 bytes of angle tables plus 52 bytes
+ * array holds (about (Nx + Ny) * N * 4 bytes of angle tables plus 4 bytes
  * per point, with Nx, Ny rounded up to 64 and N to 32) -- nothing is
  * launched then; CGH_ERR_CUDA if a CUDA call fails. */
 cgh_status cgh_forward_noalloc(const float *points, const float *A,
@@ -232,7 +257,9 @@ typedef struct {
                               degree-6 polynomial; 2: packed,
                               degree-5 polynomial; 3: as 2 with the
                               polynomial pixel pairs spread over the
-                              thread's block                        */
+                              thread's block; 4, 5: as 3 with
+                              poly_pixels + 2 polynomial pixels for
+                              every second (4) or fourth (5) point  */
 } cgh_direct_tile;
 
 /* How the direct kernel spreads its pixel tiles over the SMs (a scheduling

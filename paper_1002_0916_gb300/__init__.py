@@ -7,7 +7,7 @@ built library, or calling it without a CUDA device, raises.
 
 The functions mirror the C ABI in ``include/cgh.h`` and keep its names:
 ``cgh_create``, ``cgh_destroy``, ``cgh_forward``, ``cgh_forward_host``,
-``cgh_backward``, ``cgh_batch``, ``cgh_tune``, ``cgh_last_device_status``,
+``cgh_forward_host_async``, ``cgh_host_wait``, ``cgh_backward``, ``cgh_batch``, ``cgh_tune``, ``cgh_last_device_status``,
 ``cgh_launch_count``, ``cgh_status_string``, plus the autograd wrapper
 ``CGHFunction``.  Tensors are PyTorch CUDA tensors (float32, contiguous);
 PyTorch supplies device memory and the current stream, nothing else.
@@ -31,7 +31,8 @@ __all__ = [
     "cgh_debug_gemm", "CGHFunction", "default_handle", "KERNELS",
     "cgh_kernel_timing", "cgh_kernel_time", "cgh_tune_batch",
     "cgh_kernel_timing_mask", "cgh_set_gemm_tiles", "GEMM_TILES",
-    "cgh_debug_pipe_rates", "cgh_direct_tile_for",
+    "cgh_debug_pipe_rates", "cgh_direct_tile_for", "cgh_forward_host_async",
+    "cgh_host_wait",
 ]
 
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
@@ -80,6 +81,8 @@ def _load():
     L.cgh_destroy.argtypes = [vp]
     L.cgh_forward.argtypes = [vp, fp, fp, fp, ci, cd, cd, ci, ci, fp, ci, vp]
     L.cgh_forward_host.argtypes = L.cgh_forward.argtypes
+    L.cgh_forward_host_async.argtypes = L.cgh_forward.argtypes
+    L.cgh_host_wait.argtypes = [vp, vp]
     L.cgh_backward.argtypes = [vp, fp, fp, fp, ci, cd, cd, ci, ci, fp, fp, fp,
                                fp, ci, vp]
     L.cgh_batch.argtypes = [vp, ctypes.POINTER(_Problem), ci, ci, vp]
@@ -116,7 +119,7 @@ def _load():
     L.cgh_kernel_time.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_uint64)]
     for name in ("cgh_create", "cgh_destroy", "cgh_forward", "cgh_forward_host",
-                 "cgh_backward", "cgh_batch", "cgh_direct_tile_get",
+                 "cgh_forward_host_async", "cgh_host_wait", "cgh_backward", "cgh_batch", "cgh_direct_tile_get",
                  "cgh_set_direct_tile", "cgh_tune", "cgh_last_device_status",
                  "cgh_debug_gemm", "cgh_kernel_timing", "cgh_kernel_time"):
         getattr(L, name).restype = ci
@@ -230,32 +233,53 @@ def cgh_forward(points, A, z, lam: float, p: float, Nx: int, Ny: int, *,
     return out
 
 
+def _host_ptr(a, name, n):
+    import numpy as np
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or str(a.dtype) != "torch.float32" or not a.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float32 host tensor")
+        if a.numel() != n:
+            raise ValueError(f"{name} must have {n} elements")
+        return a.data_ptr() if n else None
+    a = np.asarray(a)
+    if a.dtype != np.float32 or not a.flags.c_contiguous or a.size != n:
+        raise TypeError(f"{name} must be contiguous float32 with {n} elements")
+    return a.ctypes.data if n else None
+
+
+def _forward_host(entry, points, A, z, lam, p, Nx, Ny, out, method, handle, stream):
+    import numpy as np
+    N = int(A.numel() if hasattr(A, "numel") else np.asarray(A).size)
+    st = getattr(_L(), entry)(handle, _host_ptr(points, "points", 2 * N),
+                              _host_ptr(A, "A", N), _host_ptr(z, "z", N), N,
+                              float(lam), float(p), int(Nx), int(Ny),
+                              _host_ptr(out, "out", Nx * Ny), _method(method),
+                              _stream_ptr(stream))
+    _check(handle, st, entry)
+    return out
+
+
 def cgh_forward_host(points, A, z, lam: float, p: float, Nx: int, Ny: int, *,
                      out, method="direct", handle, stream=None):
     """cgh_forward from host buffers (numpy arrays or CPU tensors, float32,
     contiguous; pinned memory is fastest).  Synchronises the stream."""
-    import numpy as np
+    return _forward_host("cgh_forward_host", points, A, z, lam, p, Nx, Ny, out,
+                         method, handle, stream)
 
-    def hptr(a, name, n):
-        if hasattr(a, "data_ptr"):
-            if a.is_cuda or str(a.dtype) != "torch.float32" or not a.is_contiguous():
-                raise TypeError(f"{name} must be a contiguous float32 host tensor")
-            if a.numel() != n:
-                raise ValueError(f"{name} must have {n} elements")
-            return a.data_ptr() if n else None
-        a = np.asarray(a)
-        if a.dtype != np.float32 or not a.flags.c_contiguous or a.size != n:
-            raise TypeError(f"{name} must be contiguous float32 with {n} elements")
-        return a.ctypes.data if n else None
 
-    N = int(A.numel() if hasattr(A, "numel") else np.asarray(A).size)
-    st = _L().cgh_forward_host(handle, hptr(points, "points", 2 * N),
-                              hptr(A, "A", N), hptr(z, "z", N), N, float(lam),
-                              float(p), int(Nx), int(Ny),
-                              hptr(out, "out", Nx * Ny), _method(method),
-                              _stream_ptr(stream))
-    _check(handle, st, "cgh_forward_host")
-    return out
+def cgh_forward_host_async(points, A, z, lam: float, p: float, Nx: int, Ny: int,
+                           *, out, method="direct", handle, stream=None):
+    """cgh_forward_host without the synchronisation: every buffer must be a
+    pinned CPU tensor (or page-locked array); ``out`` is complete after
+    ``cgh_host_wait(handle, stream)``.  Keep the inputs unchanged until then."""
+    return _forward_host("cgh_forward_host_async", points, A, z, lam, p, Nx, Ny,
+                         out, method, handle, stream)
+
+
+def cgh_host_wait(handle, stream=None):
+    """Wait for ``stream`` and for the host copies of earlier
+    ``cgh_forward_host_async`` calls of ``handle``."""
+    _check(handle, _L().cgh_host_wait(handle, _stream_ptr(stream)), "cgh_host_wait")
 
 
 # ------------------------------------------------------------ backward

@@ -142,7 +142,7 @@ cgh_status cgh_ctx::forward_direct(const float *points, const float *A,
     unsigned *count =
         nsplit ? (unsigned *)(base + rec_b + tab_b + amp_b + part_b) : nullptr;
 
-    {
+    if (!direct_fused_tables) {
         TimedLaunch tl(this, CGH_K_PROLOGUE, s);
         cudaError_t e = launch_prologue(points, A, z, N, Npad, lambda, p, rec,
                                         d_status, s);
@@ -150,9 +150,15 @@ cgh_status cgh_ctx::forward_direct(const float *points, const float *A,
         tl.done();
     }
     {
+        // by default the tables kernel builds the point records itself
         TimedLaunch tl(this, CGH_K_DIRECT_TABLES, s);
-        cudaError_t e = launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp,
-                                             count, nsplit, s);
+        cudaError_t e =
+            direct_fused_tables
+                ? launch_direct_tables_fused(
+                      PointSource{points, A, z, N, lambda, p, d_status}, Npad, Nx, Ny,
+                      t, phx, phy, amp, count, nsplit, s)
+                : launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp, count,
+                                       nsplit, s);
         if (e != cudaSuccess) return cuda_fail(e, "direct tables launch");
         tl.done();
     }
@@ -247,7 +253,7 @@ cgh_status cgh_ctx::forward(const float *points, const float *A,
 
 // ------------------------------------------------------------- release
 void cgh_ctx::release_all() {
-    for (Buffer *b : {&ws, &ws2, &io, &part, &meta, &bws}) {
+    for (Buffer *b : {&ws, &ws2, &io, &part, &meta, &bws, &hout[0], &hout[1]}) {
         if (b->ptr) cudaFree(b->ptr);
         b->ptr = nullptr;
         b->bytes = 0;
@@ -262,6 +268,14 @@ void cgh_ctx::release_all() {
     if (host_stage) cudaFreeHost(host_stage);
     host_stage = nullptr;
     host_stage_bytes = 0;
+    for (int k = 0; k < 2; ++k) {
+        if (hout_ready[k]) cudaEventDestroy(hout_ready[k]);
+        if (hout_copied[k]) cudaEventDestroy(hout_copied[k]);
+        hout_ready[k] = hout_copied[k] = nullptr;
+        hout_pending[k] = false;
+    }
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    copy_stream = nullptr;
 }
 
 // --------------------------------------------------------- kernel timing
@@ -380,6 +394,8 @@ cgh_status cgh_create(cgh_handle *out, int device) {
         if (v >= CGH_GEMM_AUTO && v <= CGH_GEMM_PAIRS) h->gemm_tiles = v;
     }
     if (const char *f = getenv("CGH_BWD_STAGED")) h->bwd_staged = atoi(f) != 0;
+    if (const char *f = getenv("CGH_DIRECT_FUSED_TABLES"))
+        h->direct_fused_tables = atoi(f) != 0;
     if (const char *f = getenv("CGH_BWD_POLY")) {
         const int v = atoi(f);
         if (v == 0 || v == 4 || v == 6) h->bwd_poly = v;
@@ -483,6 +499,78 @@ cgh_status cgh_forward_host(cgh_handle h, const float *points_host,
     }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return h->cuda_fail(e, "cudaStreamSynchronize");
+    return CGH_OK;
+}
+
+cgh_status cgh_forward_host_async(cgh_handle h, const float *points_host,
+                                  const float *A_host, const float *z_host,
+                                  int N, double lambda, double p, int Nx,
+                                  int Ny, float *out_host, int method,
+                                  void *stream) {
+    NvtxRange range("cgh_forward_host_async");
+    if (!h) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    h->err[0] = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    cgh_status st = h->check_problem(points_host, A_host, z_host, N, lambda, p,
+                                     Nx, Ny, out_host);
+    if (st) return st;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return h->fail(CGH_ERR_UNSUPPORTED,
+                       "cgh_forward_host_async cannot run inside stream capture");
+    const float *m_pts = N > 0 ? (const float *)mapped_device_ptr(points_host) : nullptr;
+    const float *m_A = N > 0 ? (const float *)mapped_device_ptr(A_host) : nullptr;
+    const float *m_z = N > 0 ? (const float *)mapped_device_ptr(z_host) : nullptr;
+    float *m_out = (float *)mapped_device_ptr(out_host);
+    if ((N > 0 && (!m_pts || !m_A || !m_z)) || !m_out)
+        return h->fail(CGH_ERR_INVALID_ARG,
+                       "cgh_forward_host_async needs page-locked, mapped host buffers");
+    const bool progressive = method == CGH_DIRECT_FP32 || method == CGH_NAIVE_FP32 ||
+                             method == CGH_RECUR_FP32 || method == CGH_SEP_FP32;
+    if (progressive)
+        return h->forward(m_pts, m_A, m_z, N, lambda, p, Nx, Ny, m_out, method, s);
+
+    cudaError_t e = cudaSuccess;
+    if (!h->copy_stream) {
+        e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&h->hout_ready[k], cudaEventDisableTiming);
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&h->hout_copied[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return h->cuda_fail(e, "copy stream");
+    }
+    const int k = h->hout_next;
+    // the copy out of this buffer two calls ago must be done before the new
+    // output overwrites it (a device-side wait on the caller's stream)
+    if (h->hout_pending[k]) e = cudaStreamWaitEvent(s, h->hout_copied[k], 0);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaStreamWaitEvent");
+    const size_t out_b = (size_t)Nx * Ny * sizeof(float);
+    // (growing the buffer frees the old one: cudaFree waits for the device)
+    st = h->ensure(h->hout[k], out_b, s, "asynchronous host-call output");
+    if (st) return st;
+    float *d_out = (float *)h->hout[k].ptr;
+    st = h->forward(m_pts, m_A, m_z, N, lambda, p, Nx, Ny, d_out, method, s);
+    if (st) return st;
+    e = cudaEventRecord(h->hout_ready[k], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->hout_ready[k], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_host, d_out, out_b, cudaMemcpyDeviceToHost, h->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->hout_copied[k], h->copy_stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "device-to-host copy");
+    h->hout_pending[k] = true;
+    h->hout_next = k ^ 1;
+    return CGH_OK;
+}
+
+cgh_status cgh_host_wait(cgh_handle h, void *stream) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess && h->copy_stream) e = cudaStreamSynchronize(h->copy_stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cgh_host_wait");
+    h->hout_pending[0] = h->hout_pending[1] = false;
     return CGH_OK;
 }
 

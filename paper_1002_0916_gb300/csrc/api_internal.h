@@ -41,6 +41,16 @@ struct cgh_ctx {
     Buffer meta;  // small per-call metadata (tensor maps, work lists)
     Buffer bws;   // batch workspace: per-problem records and tables
 
+    // cgh_forward_host_async: two device output buffers used in turn, the
+    // copy stream, and per buffer the events after its output was computed
+    // (caller's stream) and after its copy to the host (copy stream)
+    Buffer hout[2];
+    int hout_next = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t hout_ready[2] = {nullptr, nullptr};
+    cudaEvent_t hout_copied[2] = {nullptr, nullptr};
+    bool hout_pending[2] = {false, false};
+
     // batch: pinned staging of the work list, a private capture stream and
     // the instantiated graph of the last batch geometry
     void *host_stage = nullptr;
@@ -72,6 +82,9 @@ struct cgh_ctx {
     // direct adjoint: G staged through shared memory by TMA where its layout
     // allows (1) or read row by row from global memory (0); CGH_BWD_STAGED
     int bwd_staged = 1;
+    // direct forward: the tables kernel builds the point records itself (1)
+    // or reads them from a prologue launch (0); CGH_DIRECT_FUSED_TABLES
+    int direct_fused_tables = 1;
     // stage shape of the FP32 separable product (index into the compiled
     // shapes; 1 = 32 values of k x 2 stages, the fastest measured);
     // CGH_SIMT_STAGE at cgh_create

@@ -188,6 +188,18 @@ cudaError_t launch_direct_tables(const PointRec *rec, int Npad, int Nx, int Ny,
                                  const DirectTile &t, float *phx, float *phy,
                                  float *amp, unsigned *zero, int nzero,
                                  cudaStream_t s);
+// The caller's point arrays, for kernels that build the records themselves.
+struct PointSource {
+    const float *points, *A, *z;
+    int N;
+    double lambda, p;
+    unsigned *status;
+};
+// The same tables with the records built inside the kernel (no prologue).
+cudaError_t launch_direct_tables_fused(const PointSource &src, int Npad, int Nx,
+                                       int Ny, const DirectTile &t, float *phx,
+                                       float *phy, float *amp, unsigned *zero,
+                                       int nzero, cudaStream_t s);
 // Tail split of the direct kernel: `tiles` pixel tiles, those from `tail`
 // on each cut into m chunks of point stages (tail == tiles: none).
 struct DirectSplit {

@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "direct_tile.cuh"
+#include "point_rec.cuh"
 
 namespace cgh {
 
@@ -35,27 +36,37 @@ namespace cgh {
 // One block per DT_POINTS points (grid x) and 256 pixel columns/rows (grid
 // y) of the concatenated x and y ranges: the records are staged in shared
 // memory once, each thread then writes its coordinate for every point.
+// FUSE: the block builds its DT_POINTS records itself from the caller's
+// points (step A1, as in prologue.cu) instead of reading them from `rec`;
+// each record is then built once per block row of grid y, a few FP64
+// operations each, which costs less than a separate kernel in the chain.
 constexpr int DT_POINTS = 16;
 
+template <bool FUSE>
 __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
-                                     int Npad, int TX, int TY, int nxt,
-                                     int nyt, float *__restrict__ phx,
+                                     PointSource src, int Npad, int TX, int TY,
+                                     int nxt, int nyt, float *__restrict__ phx,
                                      float *__restrict__ phy,
                                      float *__restrict__ amp,
                                      unsigned *__restrict__ zero, int nzero) {
     __shared__ PointRec srec[DT_POINTS];
-    pdl_wait();  // the records come from the kernel before
+    pdl_wait();  // the records (or the caller's points) come from the kernel before
     pdl_trigger();
     // the split schedule's per-tile arrival counters start at zero (every
-    // earlier kernel on the stream has finished: the prologue before this
-    // launch waits for them)
+    // earlier kernel on the stream has finished: pdl_wait above)
     if (blockIdx.x == 0)
         for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < nzero;
              k += gridDim.y * blockDim.x)
             zero[k] = 0u;
     const int j0 = blockIdx.x * DT_POINTS;
-    if (threadIdx.x < DT_POINTS && j0 + (int)threadIdx.x < Npad)
-        srec[threadIdx.x] = rec[j0 + threadIdx.x];
+    if (threadIdx.x < DT_POINTS && j0 + (int)threadIdx.x < Npad) {
+        if constexpr (FUSE)
+            srec[threadIdx.x] =
+                make_point_rec(src.points, src.A, src.z, src.N, j0 + threadIdx.x,
+                               src.lambda, src.p, src.status);
+        else
+            srec[threadIdx.x] = rec[j0 + threadIdx.x];
+    }
     __syncthreads();
     const int u = blockIdx.y * blockDim.x + threadIdx.x;
     const int nx = nxt * TX, ny = nyt * TY;
@@ -210,15 +221,34 @@ size_t direct_phase_table_floats(const DirectTile &t, int Npad, int Nx,
     return nxt * Npad * t.tx + nyt * Npad * t.ty;
 }
 
+static cudaError_t launch_tables(const PointRec *rec, const PointSource *src,
+                                 int Npad, int Nx, int Ny, const DirectTile &t,
+                                 float *phx, float *phy, float *amp,
+                                 unsigned *zero, int nzero, cudaStream_t s) {
+    int nxt = (Nx + t.tx - 1) / t.tx, nyt = (Ny + t.ty - 1) / t.ty;
+    const int span = nxt * t.tx + nyt * t.ty;  // <= 65536 + 2 tiles
+    dim3 grid((Npad + DT_POINTS - 1) / DT_POINTS, (span + 255) / 256);
+    if (src)
+        return launch_dependent(direct_tables_kernel<true>, grid, dim3(256), 0, s,
+                                (const PointRec *)nullptr, *src, Npad, t.tx, t.ty,
+                                nxt, nyt, phx, phy, amp, zero, nzero);
+    return launch_dependent(direct_tables_kernel<false>, grid, dim3(256), 0, s, rec,
+                            PointSource{}, Npad, t.tx, t.ty, nxt, nyt, phx, phy, amp,
+                            zero, nzero);
+}
+
 cudaError_t launch_direct_tables(const PointRec *rec, int Npad, int Nx, int Ny,
                                  const DirectTile &t, float *phx, float *phy,
                                  float *amp, unsigned *zero, int nzero,
                                  cudaStream_t s) {
-    int nxt = (Nx + t.tx - 1) / t.tx, nyt = (Ny + t.ty - 1) / t.ty;
-    const int span = nxt * t.tx + nyt * t.ty;  // <= 65536 + 2 tiles
-    dim3 grid((Npad + DT_POINTS - 1) / DT_POINTS, (span + 255) / 256);
-    return launch_dependent(direct_tables_kernel, grid, dim3(256), 0, s, rec, Npad,
-                            t.tx, t.ty, nxt, nyt, phx, phy, amp, zero, nzero);
+    return launch_tables(rec, nullptr, Npad, Nx, Ny, t, phx, phy, amp, zero, nzero, s);
+}
+
+cudaError_t launch_direct_tables_fused(const PointSource &src, int Npad, int Nx,
+                                       int Ny, const DirectTile &t, float *phx,
+                                       float *phy, float *amp, unsigned *zero,
+                                       int nzero, cudaStream_t s) {
+    return launch_tables(nullptr, &src, Npad, Nx, Ny, t, phx, phy, amp, zero, nzero, s);
 }
 
 DirectSplit direct_split_plan(int tile_index, int sm_count, int Npad, int Nx,

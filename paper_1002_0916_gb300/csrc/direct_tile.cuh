@@ -17,7 +17,9 @@ namespace cgh {
 // order at the end), and PK: 0 scalar, 1 packed FP32x2 arithmetic on pixel
 // pairs along x (half the issue slots for the adds and FMAs), 2 packed with
 // the degree-5 polynomial, 3 as 2 with the polynomial pixel pairs spread over
-// the thread's block instead of leading it.  Every shape has 256
+// the thread's block instead of leading it, 4 and 5 as 3 with one pixel pair
+// more on the polynomial for every second point (4) or every fourth point
+// (5) -- average shares between NP and NP + 2 pixels.  Every shape has 256
 // threads per CTA.
 #define CGH_DIRECT_TILES(X)                \
     X(64, 64, 4, 4, 32, 3, 4, 1, 0)        \
@@ -40,7 +42,9 @@ namespace cgh {
     X(32, 32, 4, 4, 64, 3, 6, 4, 2)        \
     X(32, 32, 4, 4, 32, 3, 4, 4, 2)        \
     X(32, 32, 4, 4, 64, 3, 4, 4, 3)        \
-    X(32, 32, 4, 4, 64, 3, 6, 4, 3)
+    X(32, 32, 4, 4, 64, 3, 6, 4, 3)        \
+    X(32, 32, 4, 4, 64, 3, 4, 4, 4)        \
+    X(32, 32, 4, 4, 64, 3, 4, 4, 5)
 
 // ------------------------------------------------------------- tables
 // Entries of the per-axis angle tables of one problem: x angles laid out
@@ -223,22 +227,76 @@ template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G,
 struct DirectTileLoop {
     // PKV: 0 scalar arithmetic, 1 packed FP32x2 with the degree-6 polynomial,
     // 2 packed with the degree-5 polynomial, 3 as 2 with the polynomial pairs
-    // interleaved
+    // interleaved, 4 and 5 as 3 with one extra polynomial pair on every
+    // second (4) or fourth (5) point
     static constexpr bool PK = PKV != 0;
+    static constexpr int NPAIRS = VX * VY / 2;
+    // points per period of the polynomial pattern
+    static constexpr int PERIOD = PKV == 4 ? 2 : PKV == 5 ? 4 : 1;
     static_assert(NP >= 0 && NP <= VX * VY, "polynomial pixels per thread");
     static_assert(!PK || NP % 2 == 0, "packed pairs take the polynomial together");
+    static_assert(PKV < 4 || (NP / 2 + 1 <= NPAIRS && (PT / G) % PERIOD == 0),
+                  "the extra polynomial pair fits and the periods tile a stage");
     using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
     using Acc = DirectAcc<VY, VX, PK>;
 
-    // Packed tiles: which pixel pairs take the polynomial -- the first NP / 2
-    // (PKV 1, 2), or NP / 2 pairs spread evenly over the thread's pixels so
-    // that polynomial and MUFU work alternate in the instruction stream (3).
-    static constexpr bool is_poly_pair(int pair) {
-        constexpr int npairs = VX * VY / 2, npoly = NP / 2;
-        if (PKV != 3) return pair < npoly;
-        if (npoly == 0) return false;
-        constexpr int spread = npairs / (npoly > 0 ? npoly : 1);
+    // `npoly` pairs of the thread's NPAIRS spread evenly over its pixels
+    static constexpr bool spread_pair(int pair, int npoly) {
+        if (npoly <= 0) return false;
+        const int spread = NPAIRS / npoly;
         return pair % spread == 0 && pair / spread < npoly;
+    }
+
+    // Packed tiles: which pixel pairs take the polynomial for the point at
+    // position r of the pattern's period -- the first NP / 2 (PKV 1, 2), or
+    // NP / 2 pairs spread evenly over the thread's pixels so that polynomial
+    // and MUFU work alternate in the instruction stream (3), one more on the
+    // odd points (4) or on the last point of four (5).
+    static constexpr bool is_poly_pair(int pair, int r) {
+        if (PKV == 1 || PKV == 2) return pair < NP / 2;
+        const bool extra = (PKV == 4 && (r & 1)) || (PKV == 5 && r == 3);
+        return spread_pair(pair, NP / 2 + (extra ? 1 : 0));
+    }
+
+    // acc += A_q cos(theta_x + theta_y) over the thread's pixels for point q
+    // of the stage (pattern position R).
+    template <int R>
+    __device__ __forceinline__ static void point_step(Acc &acc, const float *sx,
+                                                      const float *sy, float a,
+                                                      int q) {
+        float vx[VX], vy[VY];
+        VecLoad<VX>::ld(vx, sx + q * TX);
+        VecLoad<VY>::ld(vy, sy + q * TY);
+        if constexpr (PK) {
+            const float2 a2 = make_float2(a, a), na2 = make_float2(-a, -a);
+#pragma unroll
+            for (int i = 0; i < VY; ++i) {
+                const float2 y2 = make_float2(vy[i], vy[i]);
+#pragma unroll
+                for (int k = 0; k < VX; k += 2) {
+                    const float2 th = __fadd2_rn(make_float2(vx[k], vx[k + 1]), y2);
+                    float2 &ac = acc.v[i][k >> 1];
+                    if (is_poly_pair((i * VX + k) / 2, R))
+                        ac = __ffma2_rn(na2, neg_cos_poly2<PKV == 1 ? 6 : 5>(th), ac);
+                    else
+                        ac = __ffma2_rn(a2, make_float2(__cosf(th.x), __cosf(th.y)), ac);
+                }
+            }
+        } else {
+            // the first NP pixels of the thread take the FMA-pipe polynomial,
+            // the rest the MUFU cosine (compile-time split)
+#pragma unroll
+            for (int i = 0; i < VY; ++i)
+#pragma unroll
+                for (int k = 0; k < VX; ++k) {
+                    const float th = vx[k] + vy[i];
+                    float &ac = acc.v[i][k];
+                    if (i * VX + k < NP)
+                        ac = fmaf(-a, neg_cos_poly(th), ac);
+                    else
+                        ac = fmaf(a, __cosf(th), ac);
+                }
+        }
     }
 
     __device__ static void issue(float *smem, uint64_t *full, const float *gx,
@@ -283,44 +341,26 @@ struct DirectTileLoop {
                 const float *sx = st + tx * VX;
                 const float *sy = st + S::SX + ty * VY;
                 const float *sa = st + S::SX + S::SY;
+                const int q0 = grp * S::PG;
+                // (the amplitudes of a period's points: one broadcast load;
+                // q0 and the stage offsets are multiples of 4 floats)
+                if constexpr (PERIOD == 1) {
 #pragma unroll 2
-                for (int q = grp * S::PG; q < (grp + 1) * S::PG; ++q) {
-                    const float a = sa[q];
-                    float vx[VX], vy[VY];
-                    VecLoad<VX>::ld(vx, sx + q * TX);
-                    VecLoad<VY>::ld(vy, sy + q * TY);
-                    // the first NP pixels of the thread take the FMA-pipe
-                    // polynomial, the rest the MUFU cosine (compile-time split)
-                    if constexpr (PK) {
-                        const float2 a2 = make_float2(a, a), na2 = make_float2(-a, -a);
-#pragma unroll
-                        for (int i = 0; i < VY; ++i) {
-                            const float2 y2 = make_float2(vy[i], vy[i]);
-#pragma unroll
-                            for (int k = 0; k < VX; k += 2) {
-                                const float2 th =
-                                    __fadd2_rn(make_float2(vx[k], vx[k + 1]), y2);
-                                float2 &ac = acc.v[i][k >> 1];
-                                if (is_poly_pair((i * VX + k) / 2))
-                                    ac = __ffma2_rn(na2, neg_cos_poly2<PKV == 1 ? 6 : 5>(th),
-                                                    ac);
-                                else
-                                    ac = __ffma2_rn(
-                                        a2, make_float2(__cosf(th.x), __cosf(th.y)), ac);
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < VY; ++i)
-#pragma unroll
-                            for (int k = 0; k < VX; ++k) {
-                                const float th = vx[k] + vy[i];
-                                float &ac = acc.v[i][k];
-                                if (i * VX + k < NP)
-                                    ac = fmaf(-a, neg_cos_poly(th), ac);
-                                else
-                                    ac = fmaf(a, __cosf(th), ac);
-                            }
+                    for (int q = q0; q < q0 + S::PG; ++q)
+                        point_step<0>(acc, sx, sy, sa[q], q);
+                } else if constexpr (PERIOD == 2) {
+                    for (int q = q0; q < q0 + S::PG; q += 2) {
+                        const float2 a = *reinterpret_cast<const float2 *>(sa + q);
+                        point_step<0>(acc, sx, sy, a.x, q);
+                        point_step<1>(acc, sx, sy, a.y, q + 1);
+                    }
+                } else {
+                    for (int q = q0; q < q0 + S::PG; q += 4) {
+                        const float4 a = *reinterpret_cast<const float4 *>(sa + q);
+                        point_step<0>(acc, sx, sy, a.x, q);
+                        point_step<1>(acc, sx, sy, a.y, q + 1);
+                        point_step<2>(acc, sx, sy, a.z, q + 2);
+                        point_step<3>(acc, sx, sy, a.w, q + 3);
                     }
                 }
             }

@@ -10,8 +10,9 @@
 // and status word are allocated with cudaMalloc), so this entry point takes
 // no handle at all.
 //
-// Where its scratch lives: the per-point records, the per-axis angle tables
-// and a status word of the direct path are carved out of one file-scope
+// Where its scratch lives: the per-axis angle tables, the amplitudes and a
+// status word of the direct path (whose tables kernel builds the per-point
+// records in shared memory) are carved out of one file-scope
 // __device__ array of CGH_NOALLOC_SCRATCH_BYTES.  That array exists on every
 // GPU on which this library's device code is loaded, for the life of the
 // process.  Its device address is looked up with cudaGetSymbolAddress the
@@ -82,11 +83,10 @@ extern "C" cgh_status cgh_forward_noalloc(const float *points, const float *A,
     const DirectTile t = direct_tile_get(tile_index);
     const int Npad = pad_to(N, t.pt);
     const size_t status_b = 256;
-    const size_t rec_b = align256((size_t)Npad * sizeof(PointRec));
     const size_t tab_b = align256(direct_phase_table_floats(t, Npad, Nx, Ny) *
                                   sizeof(float));
     const size_t amp_b = align256((size_t)Npad * sizeof(float));
-    if (status_b + rec_b + tab_b + amp_b > (size_t)CGH_NOALLOC_SCRATCH_BYTES)
+    if (status_b + tab_b + amp_b > (size_t)CGH_NOALLOC_SCRATCH_BYTES)
         return CGH_ERR_UNSUPPORTED;  // this frame needs more scratch than exists
 
     int dev = 0;
@@ -103,19 +103,17 @@ extern "C" cgh_status cgh_forward_noalloc(const float *points, const float *A,
     cudaStream_t s = (cudaStream_t)stream;
     char *b = (char *)base;
     unsigned *status = (unsigned *)b;
-    PointRec *rec = (PointRec *)(b + status_b);
     const int nxt = (Nx + t.tx - 1) / t.tx;
-    float *phx = (float *)(b + status_b + rec_b);
+    float *phx = (float *)(b + status_b);
     float *phy = phx + (size_t)nxt * Npad * t.tx;
-    float *amp = (float *)(b + status_b + rec_b + tab_b);
+    float *amp = (float *)(b + status_b + tab_b);
 
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned), s);
     if (e == cudaSuccess && N == 0)
         e = cudaMemsetAsync(out, 0, (size_t)Nx * Ny * sizeof(float), s);
     if (e == cudaSuccess && N > 0) {
-        e = launch_prologue(points, A, z, N, Npad, lambda, p, rec, status, s);
-        if (e == cudaSuccess)
-            e = launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp, nullptr, 0, s);
+        e = launch_direct_tables_fused(PointSource{points, A, z, N, lambda, p, status},
+                                       Npad, Nx, Ny, t, phx, phy, amp, nullptr, 0, s);
         if (e == cudaSuccess)
             e = launch_direct_forward(tile_index, phx, phy, amp, Npad, Nx, Ny, out,
                                       direct_split_plan(tile_index, 0, Npad, Nx,

@@ -53,7 +53,9 @@ def test_tile_registry(cg):
     for tx, ty, vx, vy, pt, np_, g, pk in tiles:
         assert tx % vx == 0 and ty % vy == 0 and pt % (4 * g) == 0
         assert g * (tx // vx) * (ty // vy) == 256 and 0 <= np_ <= vx * vy
-        assert pk in (0, 1, 2, 3) and (pk == 0 or (vx % 2 == 0 and np_ % 2 == 0))
+        assert pk in (0, 1, 2, 3, 4, 5) and (pk == 0 or (vx % 2 == 0 and np_ % 2 == 0))
+        if pk >= 4:   # one extra polynomial pair on every second or fourth point
+            assert np_ + 2 <= vx * vy and (pt // g) % (2 if pk == 4 else 4) == 0
 
 
 def test_null_handle_is_rejected(cg):

@@ -194,7 +194,7 @@ def test_launch_count_and_autotune(cg, h, oracle_mod):
     c = make_cloud(5, 300, 500, 300, integer=True, zlo=0.5, zhi=1.0,
                    lam=532e-9, p=8e-6)
     _fwd(cg, h, c)
-    assert cg.cgh_launch_count(h) - n0 == 3   # prologue, tables, direct
+    assert cg.cgh_launch_count(h) - n0 == 2   # tables (records built inside), direct
     tile = cg.cgh_tune(h, c.N, c.Nx, c.Ny)
     assert tile in cg.cgh_direct_tiles()
     err = max_abs(_fwd(cg, h, c), oracle_mod.forward(c))
@@ -260,3 +260,32 @@ def test_direct_tile_query(cg, h):
     assert cg.cgh_direct_tile_for(h, 200, 96, 64) == tuned
     with pytest.raises(cg.CGHError):
         cg.cgh_direct_tile_for(h, 0, 8, 8)
+
+
+def test_fused_records_match_prologue(cg, oracle_mod, monkeypatch):
+    """The tables kernel that builds the point records itself gives the same
+    hologram, bit for bit, as the prologue launch plus tables, and raises the
+    same bad-point status."""
+    import torch
+    c = make_cloud(71, 500, 300, 170, integer=False, zlo=0.2, zhi=0.9,
+                   lam=633e-9, p=6.4e-6)
+    monkeypatch.setenv("CGH_DIRECT_FUSED_TABLES", "0")
+    h0 = cg.cgh_create(0)
+    monkeypatch.delenv("CGH_DIRECT_FUSED_TABLES")
+    h1 = cg.cgh_create(0)
+    try:
+        n0 = cg.cgh_launch_count(h0)
+        I0 = _fwd(cg, h0, c)
+        assert cg.cgh_launch_count(h0) - n0 == 3   # prologue, tables, direct
+        I1 = _fwd(cg, h1, c)
+        assert np.array_equal(I0, I1)
+        assert max_abs(I1, oracle_mod.forward(c)) <= TOL * sum_abs_A(c)
+        bad = make_cloud(72, 40, 64, 64, integer=True, zlo=0.2, zhi=0.9,
+                         lam=633e-9, p=6.4e-6)
+        bad.z[7] = -1.0
+        for hh in (h0, h1):
+            _fwd(cg, hh, bad)
+            assert cg.cgh_last_device_status(hh) == cg.CGH_ERR_INVALID_ARG
+    finally:
+        cg.cgh_destroy(h0)
+        cg.cgh_destroy(h1)
