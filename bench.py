@@ -669,7 +669,8 @@ def run_ours(args):
                 ("tile_x", "tile_y", "vec_x", "vec_y", "points_per_stage",
                  "poly_pixels", "point_groups", "packed"),
                 cg.cgh_direct_tile_for(h, c.N, c.Nx, c.Ny)))
-            cfg["gemm_tiles"] = "auto (CTA pairs above 128 rows)"
+            tiling, width = cg.cgh_gemm_plan(h, c.Nx, c.Ny)
+            cfg["gemm_tiles"] = {"tiling": tiling, "width": width}
         if args.workload == "table1":
             cfg["workload"] = ("1920x1024 pixels, N = 512, 1024, ..., 3584 points (the "
                                "paper's Table 1 sweep), otherwise the 1920x1024x1024 "

@@ -311,6 +311,13 @@ typedef enum {
  * value. */
 cgh_status cgh_set_gemm_tiles(cgh_handle h, int tiles);
 
+/* The tiling a separable forward GEMM of an Ny-row, Nx-column hologram
+ * takes on this handle under its current setting: *tiling receives
+ * CGH_GEMM_SINGLE or CGH_GEMM_PAIRS and *width the tile width (hologram
+ * columns per tile).  CGH_ERR_INVALID_ARG for a null pointer or a size
+ * below 1. */
+cgh_status cgh_gemm_plan(cgh_handle h, int Nx, int Ny, int *tiling, int *width);
+
 /* Number of direct-kernel tile shapes compiled into this library, and the
  * i-th of them (0 <= i < count). */
 int cgh_direct_tile_count(void);

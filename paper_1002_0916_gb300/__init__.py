@@ -32,7 +32,7 @@ __all__ = [
     "cgh_kernel_timing", "cgh_kernel_time", "cgh_tune_batch",
     "cgh_kernel_timing_mask", "cgh_set_gemm_tiles", "GEMM_TILES",
     "cgh_debug_pipe_rates", "cgh_direct_tile_for", "cgh_forward_host_async",
-    "cgh_host_wait",
+    "cgh_host_wait", "cgh_gemm_plan",
 ]
 
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
@@ -94,6 +94,8 @@ def _load():
     L.cgh_direct_tile_for.restype = ci
     L.cgh_set_gemm_tiles.argtypes = [vp, ci]
     L.cgh_set_gemm_tiles.restype = ci
+    L.cgh_gemm_plan.argtypes = [vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.cgh_gemm_plan.restype = ci
     L.cgh_debug_pipe_rates.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), vp]
     L.cgh_debug_pipe_rates.restype = ci
@@ -409,6 +411,15 @@ def cgh_set_gemm_tiles(h, tiles="auto"):
     tcgen05 cta_group::2) or "auto"."""
     st = _L().cgh_set_gemm_tiles(h, GEMM_TILES[tiles])
     _check(h, st, "cgh_set_gemm_tiles")
+
+
+def cgh_gemm_plan(h, Nx: int, Ny: int):
+    """(tiling, width) the separable forward GEMM of an Nx x Ny hologram
+    takes on this handle: tiling is "single" or "pairs"."""
+    t, w = ctypes.c_int(), ctypes.c_int()
+    _check(h, _L().cgh_gemm_plan(h, int(Nx), int(Ny), ctypes.byref(t), ctypes.byref(w)),
+           "cgh_gemm_plan")
+    return {v: k for k, v in GEMM_TILES.items()}[t.value], w.value
 
 
 def cgh_tune(h, N: int, Nx: int, Ny: int, method="direct", stream=None):

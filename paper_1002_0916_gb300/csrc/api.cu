@@ -684,9 +684,17 @@ cgh_status cgh_set_direct_schedule(cgh_handle h, int schedule) {
     return CGH_OK;
 }
 
+cgh_status cgh_gemm_plan(cgh_handle h, int Nx, int Ny, int *tiling, int *width) {
+    if (!h || !tiling || !width || Nx < 1 || Ny < 1) return CGH_ERR_INVALID_ARG;
+    const GemmPlan p = gemm_plan(Ny, Nx, h->gemm_tiles, h->sm_count);
+    *tiling = p.tiling;
+    *width = p.bn;
+    return CGH_OK;
+}
+
 cgh_status cgh_set_gemm_tiles(cgh_handle h, int tiles) {
     if (!h) return CGH_ERR_INVALID_ARG;
-    if (tiles != CGH_GEMM_AUTO && tiles != CGH_GEMM_SINGLE && tiles != CGH_GEMM_PAIRS)
+    if (tiles < CGH_GEMM_AUTO || tiles > CGH_GEMM_PAIRS)
         return h->fail(CGH_ERR_INVALID_ARG, "unknown GEMM tiling %d", tiles);
     h->gemm_tiles = tiles;
     return CGH_OK;

@@ -256,7 +256,14 @@ inline int gemm_k_chunks(int K, bool split) {
 }
 // umma2.cu: the same product on CTA pairs (256-row tiles over two SMs);
 // bnp = columns of a pair tile (one of the compiled widths)
-int pick_pair_n(int M, int N, int sms);
+// The pair tile width for an M x N product and its cost (SM waves x width).
+int pick_pair_n(int M, int N, int sms, double *cost = nullptr);
+// How launch_umma_gemm tiles an M x N forward product under a cgh_gemm_tiles
+// setting: CGH_GEMM_SINGLE or CGH_GEMM_PAIRS, and the tile width.
+struct GemmPlan {
+    int tiling, bn;
+};
+GemmPlan gemm_plan(int M, int N, int tiles, int sms);
 cudaError_t launch_umma_pair(const GemmOperands &op, int bnp, unsigned *status,
                              cudaStream_t s);
 struct AdjEpiArgs;

@@ -337,6 +337,16 @@ static int pick_tile_n(int M, int N, int sms) {
     return cost(112) < cost(128) ? 112 : 128;
 }
 
+GemmPlan gemm_plan(int M, int N, int tiles, int sms) {
+    // CTA pairs halve each SM's operand bytes per multiply-add; measured on
+    // the 3840 x 2160 x 16384 product 1.9x (single pass) and 1.3x (split)
+    // faster than one-CTA tiles, equal at 1920 x 1024 x 1024.  A frame of
+    // at most 128 rows would leave half of every pair tile empty.
+    const bool pairs = tiles == CGH_GEMM_PAIRS || (tiles == CGH_GEMM_AUTO && M > 128);
+    if (!pairs) return GemmPlan{CGH_GEMM_SINGLE, pick_tile_n(M, N, sms)};
+    return GemmPlan{CGH_GEMM_PAIRS, pick_pair_n(M, N, sms)};
+}
+
 cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
                              cudaStream_t s) {
     if (!gemm_operands_ok(op)) return cudaErrorInvalidValue;
@@ -360,15 +370,9 @@ cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
         return cudaSuccess;
     }
     AdjEpiArgs ea{};
-    const int sms = sm_count_of_current_device();
-    // CTA pairs halve each SM's operand bytes per multiply-add; measured on
-    // the 3840 x 2160 x 16384 product 1.9x (single pass) and 1.3x (split)
-    // faster than one-CTA tiles, equal at 1920 x 1024 x 1024.  A frame of
-    // at most 128 rows would leave half of every pair tile empty.
-    const bool pairs = op.tiles == CGH_GEMM_PAIRS ||
-                       (op.tiles == CGH_GEMM_AUTO && op.M > 128);
-    if (pairs) return launch_umma_pair(op, pick_pair_n(op.M, op.N, sms), status, s);
-    const int bn = pick_tile_n(op.M, op.N, sms);
+    const GemmPlan plan = gemm_plan(op.M, op.N, op.tiles, sm_count_of_current_device());
+    if (plan.tiling == CGH_GEMM_PAIRS) return launch_umma_pair(op, plan.bn, status, s);
+    const int bn = plan.bn;
     if (op.split)
         return bn == 112 ? launch_gemm_t<112, true, 3, 0>(op, ea, status, s)
                          : launch_gemm_t<128, true, 3, 0>(op, ea, status, s);

@@ -363,25 +363,26 @@ static cudaError_t launch_pair_t(const GemmOperands &op, unsigned *status,
 }
 
 // The pair widths compiled in (columns of one 256-row pair tile).
-static const int kPairBN[] = {112, 160, 224, 256};
+static const int kPairBN[] = {112, 144, 160, 224, 256};
 
 // Cost of a pair width: SM waves x columns per CTA (the work of one CTA is
-// proportional to its columns).
+// proportional to its columns), with a small preference for wide tiles.
 static double pair_cost(int M, int N, int bnp, int sms) {
     const long long ctas = 2LL * ((M + 255) / 256) * ((N + bnp - 1) / bnp);
-    return (double)((ctas + sms - 1) / sms) * bnp;
+    return (double)((ctas + sms - 1) / sms) * bnp / (1.0 + 0.002 * bnp);
 }
 
-int pick_pair_n(int M, int N, int sms) {
+int pick_pair_n(int M, int N, int sms, double *cost) {
     int best = kPairBN[0];
     double best_cost = 1e300;
     for (int bnp : kPairBN) {
-        const double c = pair_cost(M, N, bnp, sms) / (1.0 + 0.002 * bnp);
+        const double c = pair_cost(M, N, bnp, sms);
         if (c < best_cost) {
             best_cost = c;
             best = bnp;
         }
     }
+    if (cost) *cost = best_cost;
     return best;
 }
 
@@ -397,6 +398,7 @@ cudaError_t launch_umma_pair(const GemmOperands &op, int bnp, unsigned *status,
     if (op.split) {
         switch (bnp) {
         case 112: return launch_pair_t<112, true, 4>(op, status, s);
+        case 144: return launch_pair_t<144, true, 4>(op, status, s);
         case 160: return launch_pair_t<160, true, 4>(op, status, s);
         case 224: return launch_pair_t<224, true, 3>(op, status, s);
         case 256: return launch_pair_t<256, true, 3>(op, status, s);
@@ -404,6 +406,7 @@ cudaError_t launch_umma_pair(const GemmOperands &op, int bnp, unsigned *status,
     } else {
         switch (bnp) {
         case 112: return launch_pair_t<112, false, 9>(op, status, s);
+        case 144: return launch_pair_t<144, false, 8>(op, status, s);
         case 160: return launch_pair_t<160, false, 8>(op, status, s);
         case 224: return launch_pair_t<224, false, 7>(op, status, s);
         case 256: return launch_pair_t<256, false, 7>(op, status, s);

@@ -24,18 +24,29 @@ template <int CH>
 __device__ __forceinline__ void epilogue_store_row(float *drow, int col, float (&v)[CH],
                                                    const GemmArgs &g, bool vec) {
     if (vec && col + CH <= g.N) {
+        if (g.accumulate) {
+            // all of the chunk's loads before any of its stores: one memory
+            // latency per chunk instead of one per vector
+            float4 d[CH / 4];
 #pragma unroll
-        for (int i = 0; i < CH; i += 4) {
-            float4 o = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-            if (g.accumulate) {
-                const float4 d = *reinterpret_cast<const float4 *>(drow + col + i);
-                o.x += d.x;
-                o.y += d.y;
-                o.z += d.z;
-                o.w += d.w;
+            for (int i = 0; i < CH; i += 4)
+                d[i / 4] = *reinterpret_cast<const float4 *>(drow + col + i);
+#pragma unroll
+            for (int i = 0; i < CH; i += 4) {
+                d[i / 4].x += v[i];
+                d[i / 4].y += v[i + 1];
+                d[i / 4].z += v[i + 2];
+                d[i / 4].w += v[i + 3];
             }
-            *reinterpret_cast<float4 *>(drow + col + i) = o;
+#pragma unroll
+            for (int i = 0; i < CH; i += 4)
+                *reinterpret_cast<float4 *>(drow + col + i) = d[i / 4];
+            return;
         }
+#pragma unroll
+        for (int i = 0; i < CH; i += 4)
+            *reinterpret_cast<float4 *>(drow + col + i) =
+                make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
     } else {
 #pragma unroll
         for (int i = 0; i < CH; ++i)

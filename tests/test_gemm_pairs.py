@@ -34,7 +34,8 @@ def h(cg):
 @pytest.mark.parametrize("dtype", ["fp16", "bf16"])
 @pytest.mark.parametrize("M,N,K", [(256, 112, 64), (200, 300, 128), (1, 1, 64),
                                    (129, 257, 192), (1024, 1920, 2048),
-                                   (333, 129, 1024), (2160, 3840, 256)])
+                                   (333, 129, 1024), (2160, 3840, 256),
+                                   (1080, 1920, 256)])
 def test_pair_gemm_matches_fp64_product(cg, h, dtype, M, N, K):
     import torch
     tdt = {"fp16": torch.float16, "bf16": torch.bfloat16}[dtype]
@@ -123,3 +124,23 @@ def test_tiling_argument_errors(cg, h):
         cg.cgh_set_gemm_tiles(h, "bogus")
     assert cg.lib.cgh_set_gemm_tiles(h, 9) == cg.CGH_ERR_INVALID_ARG
     assert cg.lib.cgh_set_gemm_tiles(None, 0) == cg.CGH_ERR_INVALID_ARG
+
+
+
+def test_gemm_plan(cg):
+    """The tile widths the automatic plan takes: 112-column pairs at the
+    paper's 1920 x 1024 (144 CTAs on 152 SMs), 144 at 1920 x 1080 (140), 256
+    at 3840 x 2160 (two waves); one-CTA tiles for frames of at most 128 rows
+    and when asked for."""
+    hh = cg.cgh_create(0)
+    try:
+        assert cg.cgh_gemm_plan(hh, 1920, 1024) == ("pairs", 112)
+        assert cg.cgh_gemm_plan(hh, 1920, 1080) == ("pairs", 144)
+        assert cg.cgh_gemm_plan(hh, 3840, 2160) == ("pairs", 256)
+        assert cg.cgh_gemm_plan(hh, 300, 100)[0] == "single"
+        cg.cgh_set_gemm_tiles(hh, "single")
+        assert cg.cgh_gemm_plan(hh, 1920, 1024)[0] == "single"
+        with pytest.raises(cg.CGHError):
+            cg.cgh_gemm_plan(hh, 0, 10)
+    finally:
+        cg.cgh_destroy(hh)
