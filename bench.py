@@ -46,11 +46,12 @@ FP32_PER_CLK_PER_SM = 128    # FP32 lanes of the FMA pipe per SM per clock
 # instructions do two of these operations per slot.)
 MIXED_PP_PER_CLK_PER_SM = 16.0 * 14.0 / 9.0
 # The direct adjoint per update: hardware path = angle add, argument scale,
-# sin + cos (2 MUFU), 6 accumulation ops (8 FP32 ops); polynomial path =
-# add, fold, square, 5 + 5 FMA (cos and sin), times u, 6 accumulation ops
-# (20 FP32 ops, no MUFU).  FMA-pipe limit 128 / (8 + 12 s), MUFU limit
-# 16 / (2 (1 - s)): they meet at s = 2/7, 11.2 updates per clock per SM.
-ADJ_MIXED_PP_PER_CLK_PER_SM = 8.0 * 7.0 / 5.0
+# sin + cos (2 MUFU), 3 accumulations (G cos, the column's and the row's
+# G sin: 5 FP32 ops); polynomial path = add, fold, square, 5 + 5 FMA (cos
+# and sin), times u, 3 accumulations (17 FP32 ops, no MUFU).  FMA-pipe
+# limit 128 / (5 + 12 s), MUFU limit 16 / (2 (1 - s)): they meet at
+# s = 11/28, 224/17 = 13.2 updates per clock per SM.
+ADJ_MIXED_PP_PER_CLK_PER_SM = 224.0 / 17.0
 # The Eq. 2 recurrence kernel (the paper's design) per update: 1 MUFU
 # cosine, 7 issue slots (2 integer adds, shift, or, FMA to radians,
 # argument scale, accumulate): the MUFU binds at 16 updates/clk/SM.
@@ -542,8 +543,8 @@ def run_ours(args):
         elif dom == "bwd_direct":
             per_clk = ADJ_MIXED_PP_PER_CLK_PER_SM
             src = ("FMA-pipe (128 FP32 ops/clk/SM) and MUFU (16 ops/clk/SM) limits of "
-                   "the adjoint recipe: 8 FP32 ops + 2 MUFU (sin, cos) per hardware "
-                   "update, 20 FP32 ops per polynomial update, best mix 2/7 -> 11.2 "
+                   "the adjoint recipe: 5 FP32 ops + 2 MUFU (sin, cos) per hardware "
+                   "update, 17 FP32 ops per polynomial update, best mix 11/28 -> 13.2 "
                    "updates/clk/SM")
         else:
             per_clk = MIXED_PP_PER_CLK_PER_SM
@@ -560,7 +561,7 @@ def run_ours(args):
             # the same recipe bound with the measured rates in place of the
             # nominal 16 MUFU cosines and 128 FMAs per clock per SM
             m, f = pipe_rates["mufu_cos_per_clk_per_sm"], pipe_rates["fma_per_clk_per_sm"]
-            per_clk_m = {"simt": f / 2.0, "recur": m, "bwd_direct": (f + 6.0 * m) / 20.0
+            per_clk_m = {"simt": f / 2.0, "recur": m, "bwd_direct": (f + 6.0 * m) / 17.0
                          }.get(dom, (f + 6.0 * m) / 9.0)
             roof["measured_pipe_rates"] = dict(pipe_rates)
             roof["peak_from_measured_rates"] = sms * per_clk_m * NOMINAL_MAX_MHZ * 1e6 / 1e9

@@ -151,10 +151,13 @@ __global__ void adj_tables_kernel(const PointRec *__restrict__ rec, int N,
 // runs on column pairs in packed FP32x2.  NPOLY columns (pairs spread evenly
 // over the strip) take sin and cos from FMA-pipe polynomials (u = |theta| - pi: cos theta = -C(u^2),
 // sin theta = -sign(theta) u S(u^2); cos_poly.h), the others from the
-// hardware sincos (two MUFU operations): per update 8 FP32 operations and 2
-// MUFU on the hardware path, 20 FP32 operations on the polynomial path.  The
-// polynomial columns accumulate the negated sums and are subtracted at the
-// end.
+// hardware sincos (two MUFU operations).  The offset dx = x - x_j is
+// constant down a column, so the x sums of G sin(phi) dx and G sin(phi) dx^2
+// are taken as dx and dx^2 times each column's sum of G sin(phi), formed once
+// at the end: per update 5 FP32 operations and 2 MUFU on the hardware path
+// (angle add, argument scale, and the cos, column and row sums), 17 on the
+// polynomial path.  The polynomial columns accumulate negated sums, whose
+// sign is restored at the end.
 constexpr int BWD_STRIP = 16;    // pixels per column strip
 // points per CTA: 256 with G staged through shared memory (each staged row
 // serves more points), 128 reading G rows from global memory (measured:
@@ -169,48 +172,57 @@ constexpr int BWD_NP2 = BWD_STRIP / 2;
 constexpr int BWD_RB = 32;
 constexpr int BWD_NST = 4;
 
-// One thread's sums over its strip: hardware-path sums (+) and
-// polynomial-path sums (negated), per column pair.
+// One thread's sums over its strip: G cos(phi) of the hardware columns (+)
+// and of the polynomial columns (negated), G sin(phi) per column pair (the
+// polynomial pairs negated), and the y sums.
 struct BwdAcc {
-    float2 sC, sX, sXX, nC, nX, nXX;
+    float2 sC, nC;
+    float2 S[BWD_NP2];
     float sY, sYY;
 };
 
-// The x angles and offsets of the thread's strip, and the start of its
-// exact fixed-point y recurrence.
+// The x angles of the thread's strip, and the start of its exact
+// fixed-point y recurrence.
 struct BwdPoint {
-    float2 tx[BWD_NP2], dx[BWD_NP2];
+    float2 tx[BWD_NP2];
     uint64_t th, dth, d2;
-    float yj;
+    float xj, yj;
     bool valid;
 };
+
+// Polynomial column pairs, spread evenly among the hardware ones.
+template <int NPOLY>
+__device__ __forceinline__ constexpr bool bwd_poly_pair(int k) {
+    return NPOLY > 0 && k % (BWD_STRIP / (NPOLY > 0 ? NPOLY : 1)) == 0 &&
+           k / (BWD_STRIP / (NPOLY > 0 ? NPOLY : 1)) < NPOLY / 2;
+}
 
 __device__ __forceinline__ void bwd_point(const PointRec *__restrict__ rec,
                                           const float *__restrict__ points, int N,
                                           int j, int x0, BwdPoint &P, BwdAcc &acc) {
     P.valid = j < N;
     PointRec pr{};
-    float xj = 0.0f;
+    P.xj = 0.0f;
     P.yj = 0.0f;
     if (P.valid) {
         pr = rec[j];
-        xj = points[2 * j];
+        P.xj = points[2 * j];
         P.yj = points[2 * j + 1];
     }
 #pragma unroll
-    for (int k = 0; k < BWD_NP2; ++k) {
+    for (int k = 0; k < BWD_NP2; ++k)
         P.tx[k] = make_float2(
             (float)phase_hi(axis_phase(pr.c, pr.bx, pr.ax, x0 + 2 * k)) * RAD_PER_U32,
             (float)phase_hi(axis_phase(pr.c, pr.bx, pr.ax, x0 + 2 * k + 1)) * RAD_PER_U32);
-        P.dx[k] = make_float2((float)(x0 + 2 * k) - xj, (float)(x0 + 2 * k + 1) - xj);
-    }
     // y angle by the fixed-point recurrence: th(y+1) = th(y) + d(y),
     // d(y+1) = d(y) + 2c (exact modulo one turn)
     P.th = pr.ay;
     P.dth = pr.c - pr.by;
     P.d2 = 2 * pr.c;
     const float2 z2 = make_float2(0.0f, 0.0f);
-    acc.sC = acc.sX = acc.sXX = acc.nC = acc.nX = acc.nXX = z2;
+    acc.sC = acc.nC = z2;
+#pragma unroll
+    for (int k = 0; k < BWD_NP2; ++k) acc.S[k] = z2;
     acc.sY = acc.sYY = 0.0f;
 }
 
@@ -228,8 +240,7 @@ __device__ __forceinline__ void bwd_row(BwdPoint &P, int y, const float2 (&g)[BW
 #pragma unroll
     for (int k = 0; k < BWD_NP2; ++k) {
         const float2 a = __fadd2_rn(P.tx[k], ty2);
-        // polynomial pairs spread evenly among the hardware ones
-        if (NPOLY > 0 && k % (BWD_STRIP / NPOLY) == 0 && k / (BWD_STRIP / NPOLY) < NPOLY / 2) {
+        if (bwd_poly_pair<NPOLY>(k)) {
             const float2 u = make_float2(fabsf(a.x) - PI_F, fabsf(a.y) - PI_F);
             const float2 w = __fmul2_rn(u, u);
             float2 c = make_float2(COS5_C5, COS5_C5);
@@ -250,21 +261,15 @@ __device__ __forceinline__ void bwd_row(BwdPoint &P, int y, const float2 (&g)[BW
                 __int_as_float(__float_as_int(v.x) ^ (__float_as_int(a.x) & 0x80000000)),
                 __int_as_float(__float_as_int(v.y) ^ (__float_as_int(a.y) & 0x80000000)));
             acc.nC = __ffma2_rn(g[k], c, acc.nC);
-            const float2 sg = __fmul2_rn(g[k], v);
-            const float2 t = __fmul2_rn(sg, P.dx[k]);
-            acc.nX = __fadd2_rn(acc.nX, t);
-            acc.nXX = __ffma2_rn(t, P.dx[k], acc.nXX);
-            nrs = __fadd2_rn(nrs, sg);
+            acc.S[k] = __ffma2_rn(g[k], v, acc.S[k]);
+            nrs = __ffma2_rn(g[k], v, nrs);
         } else {
             float2 sv, cv;
             __sincosf(a.x, &sv.x, &cv.x);
             __sincosf(a.y, &sv.y, &cv.y);
             acc.sC = __ffma2_rn(g[k], cv, acc.sC);
-            const float2 sg = __fmul2_rn(g[k], sv);
-            const float2 t = __fmul2_rn(sg, P.dx[k]);
-            acc.sX = __fadd2_rn(acc.sX, t);
-            acc.sXX = __ffma2_rn(t, P.dx[k], acc.sXX);
-            rs = __fadd2_rn(rs, sg);
+            acc.S[k] = __ffma2_rn(g[k], sv, acc.S[k]);
+            rs = __ffma2_rn(g[k], sv, rs);
         }
     }
     const float r = (rs.x + rs.y) - (nrs.x + nrs.y);
@@ -272,15 +277,27 @@ __device__ __forceinline__ void bwd_row(BwdPoint &P, int y, const float2 (&g)[BW
     acc.sYY = fmaf(r * dy, dy, acc.sYY);
 }
 
+template <int NPOLY>
 __device__ __forceinline__ void bwd_store(const BwdPoint &P, const BwdAcc &acc, int strip,
                                           int j, int Npad, float *__restrict__ part_x,
                                           float *__restrict__ part_y) {
     if (!P.valid) return;
     float *px = part_x + ((size_t)strip * Npad + j) * 3;
     float *py = part_y + ((size_t)strip * Npad + j) * 3;
+    const int x0 = strip * BWD_STRIP;
+    // the x sums: dx and dx^2 times each column's sum of G sin(phi)
+    float sX = 0.0f, sXX = 0.0f;
+#pragma unroll
+    for (int k = 0; k < BWD_NP2; ++k) {
+        const float sgn = bwd_poly_pair<NPOLY>(k) ? -1.0f : 1.0f;
+        const float dx0 = (float)(x0 + 2 * k) - P.xj, dx1 = (float)(x0 + 2 * k + 1) - P.xj;
+        const float t0 = sgn * acc.S[k].x * dx0, t1 = sgn * acc.S[k].y * dx1;
+        sX += t0 + t1;
+        sXX = fmaf(t0, dx0, fmaf(t1, dx1, sXX));
+    }
     px[0] = (acc.sC.x + acc.sC.y) - (acc.nC.x + acc.nC.y);
-    px[1] = (acc.sX.x + acc.sX.y) - (acc.nX.x + acc.nX.y);
-    px[2] = (acc.sXX.x + acc.sXX.y) - (acc.nXX.x + acc.nXX.y);
+    px[1] = sX;
+    px[2] = sXX;
     py[0] = 0.0f;
     py[1] = acc.sY;
     py[2] = acc.sYY;
@@ -320,7 +337,7 @@ direct_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ po
         }
         bwd_row<NPOLY>(P, y, g, acc);
     }
-    bwd_store(P, acc, strip, j, Npad, part_x, part_y);
+    bwd_store<NPOLY>(P, acc, strip, j, Npad, part_x, part_y);
 }
 
 // G staged through shared memory: the CTA's 16-column strip arrives BWD_RB
@@ -400,7 +417,7 @@ direct_bwd_staged_kernel(const __grid_constant__ CUtensorMap tG,
                 mbar_wait_bounded(&full[u % BWD_NST], (uint32_t)((u / BWD_NST) & 1));
         return;
     }
-    bwd_store(P, acc, strip, j, Npad, part_x, part_y);
+    bwd_store<NPOLY>(P, acc, strip, j, Npad, part_x, part_y);
 }
 
 // ------------------------------------------------------------ reduce
