@@ -59,6 +59,10 @@ RECUR_PP_PER_CLK_PER_SM = 16.0
 # The FP32 separable product (angle addition) per update: 2 FP32
 # multiply-adds on the FMA pipe, no MUFU: 128 / 2 = 64 updates/clk/SM.
 SIMT_PP_PER_CLK_PER_SM = 64.0
+# The FP32 separable adjoint per update: 4 FP32 multiply-adds (the column
+# sums U, V and the row sums P, Q), no MUFU: 128 / 4 = 32 updates/clk/SM
+# (the row's sincos and sums, shared by 16 updates, not counted).
+BWD_SIMT_PP_PER_CLK_PER_SM = 32.0
 # The paper's Table 1 (1,920 x 1,024 pixels), times in ms, for context.
 PAPER_TABLE1 = {
     "N": [512, 1024, 1536, 2048, 2560, 3072, 3584],
@@ -378,7 +382,7 @@ def build_legs(cg, h, which, methods, dev, stream):
         pts, A, z = dev_cloud(c)
         G = torch.from_numpy(grad_field(11, c.Nx, c.Ny, scale=40.0)).to(dev)
         for m in methods:
-            if m not in ("direct", "sep_fp16x3"):
+            if m not in ("direct", "sep_fp32", "sep_fp16x3"):
                 continue
             out = torch.empty((c.Ny, c.Nx), dtype=torch.float32, device=dev)
             f_fwd = (lambda m=m, out=out: cg.cgh_forward(
@@ -392,7 +396,8 @@ def build_legs(cg, h, which, methods, dev, stream):
                             kernel=MAIN_KERNEL[m]))
             legs.append(Leg(m + "_bwd", f_bwd, c.pp, 2 * 4.0 * c.pp * mult,
                             2 if mult else 0,
-                            kernel="bwd_direct" if m == "direct" else "bwd_gemm"))
+                            kernel={"direct": "bwd_direct", "sep_fp32": "bwd_simt"}.get(
+                                m, "bwd_gemm")))
         return c, legs
     raise SystemExit(f"unknown workload {which}")
 
@@ -422,8 +427,9 @@ def run_ours(args):
     h = cg.cgh_create(local)
     stream = torch.cuda.current_stream()
     if args.methods is None:
-        args.methods = ("direct,recur,sep_fp32,sep_fp16x3" if args.workload == "table1"
-                        else "direct,sep_fp16x3")
+        args.methods = {"table1": "direct,recur,sep_fp32,sep_fp16x3",
+                        "adjoint": "direct,sep_fp32,sep_fp16x3"}.get(args.workload,
+                                                                     "direct,sep_fp16x3")
     methods = [m.strip() for m in args.methods.split(",") if m.strip()]
     c, all_legs = build_legs(cg, h, args.workload, methods, dev, stream)
     legs = []
@@ -469,7 +475,7 @@ def run_ours(args):
     # the two pipe rates the ALU rooflines are derived from, measured on this
     # device (outside the timed region)
     pipe_rates = None
-    if dom in ("direct", "naive", "batch", "bwd_direct", "recur", "simt"):
+    if dom in ("direct", "naive", "batch", "bwd_direct", "recur", "simt", "bwd_simt"):
         pipe_rates = cg.cgh_debug_pipe_rates(h, stream=stream)
     props = torch.cuda.get_device_properties(dev)
     sampler = ClockSampler(f"GPU-{props.uuid}" if getattr(props, "uuid", None)
@@ -526,7 +532,7 @@ def run_ours(args):
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
     sms = props.multi_processor_count
-    if dom in ("direct", "naive", "batch", "bwd_direct", "recur", "simt"):
+    if dom in ("direct", "naive", "batch", "bwd_direct", "recur", "simt", "bwd_simt"):
         # point-pixel updates per launch of the dominant kernel: the mean over
         # the legs it serves (each leg launches it once per step)
         dom_legs = [leg.pp for leg in legs if leg.kernel == dom]
@@ -535,6 +541,10 @@ def run_ours(args):
         if dom == "simt":
             per_clk = SIMT_PP_PER_CLK_PER_SM
             src = ("FMA-pipe limit of the FP32 angle-addition product: 2 FP32 "
+                   "multiply-adds per update, 128 per clk/SM")
+        elif dom == "bwd_simt":
+            per_clk = BWD_SIMT_PP_PER_CLK_PER_SM
+            src = ("FMA-pipe limit of the FP32 angle-addition adjoint: 4 FP32 "
                    "multiply-adds per update, 128 per clk/SM")
         elif dom == "recur":
             per_clk = RECUR_PP_PER_CLK_PER_SM
@@ -561,12 +571,12 @@ def run_ours(args):
             # the same recipe bound with the measured rates in place of the
             # nominal 16 MUFU cosines and 128 FMAs per clock per SM
             m, f = pipe_rates["mufu_cos_per_clk_per_sm"], pipe_rates["fma_per_clk_per_sm"]
-            per_clk_m = {"simt": f / 2.0, "recur": m, "bwd_direct": (f + 6.0 * m) / 17.0
-                         }.get(dom, (f + 6.0 * m) / 9.0)
+            per_clk_m = {"simt": f / 2.0, "bwd_simt": f / 4.0, "recur": m,
+                         "bwd_direct": (f + 6.0 * m) / 17.0}.get(dom, (f + 6.0 * m) / 9.0)
             roof["measured_pipe_rates"] = dict(pipe_rates)
             roof["peak_from_measured_rates"] = sms * per_clk_m * NOMINAL_MAX_MHZ * 1e6 / 1e9
             roof["frac_of_measured_rates"] = achieved / roof["peak_from_measured_rates"]
-        if dom != "simt":
+        if dom not in ("simt", "bwd_simt"):
             mufu_per_pp = 2.0 if dom == "bwd_direct" else 1.0
             roof["frac_mufu_only"] = achieved / (
                 sms * MUFU_PER_CLK_PER_SM / mufu_per_pp * NOMINAL_MAX_MHZ * 1e6 / 1e9)

@@ -166,9 +166,13 @@ cgh_status cgh_host_wait(cgh_handle h, void *stream);
  *   grad_z[j]          = (P_j A_j / z_j) sum_pix G sin(phi) r^2
  * with phi = P_j r^2, r^2 = (x_h - x_j)^2 + (y_h - y_j)^2 (derivatives of
  * Eq. 1; dP_j/dz_j = -P_j/z_j).  Any of the three outputs may be NULL to
- * skip it.  method: CGH_DIRECT_FP32 (FP32, point-owned sums, deterministic)
- * or CGH_SEP_FP16X3 (two split-FP16 tensor-core GEMMs, G V and G^T U, with
- * the pixel sums fused into their epilogues).  Errors as cgh_forward. */
+ * skip it.  method: CGH_DIRECT_FP32 (FP32, point-owned sums, deterministic),
+ * CGH_SEP_FP32 (the same point-owned FP32 sums with cos(phi) and sin(phi)
+ * expanded by angle addition into per-column sums of G cos, G sin of the
+ * row angle and per-row sums of G cos, G sin of the column angle;
+ * deterministic) or CGH_SEP_FP16X3 (two split-FP16 tensor-core GEMMs, G V and
+ * G^T U, with the pixel sums fused into their epilogues).  Other methods:
+ * CGH_ERR_INVALID_ARG.  Errors as cgh_forward. */
 cgh_status cgh_backward(cgh_handle h, const float *points, const float *A,
                         const float *z, int N, double lambda, double p,
                         int Nx, int Ny, const float *grad_out,
@@ -359,6 +363,7 @@ typedef enum {
     CGH_K_BATCH_SEP = 11,     /* separable batch (its whole graph)      */
     CGH_K_RECUR = 12,         /* Eq. 2 recurrence kernel                */
     CGH_K_SIMT = 13,          /* FP32 separable product (FMA pipe)      */
+    CGH_K_BWD_SIMT = 14,      /* FP32 separable adjoint (FMA pipe)      */
     CGH_K_COUNT = 16
 } cgh_kernel_id;
 

@@ -443,7 +443,7 @@ def cgh_launch_count(h) -> int:
 KERNELS = {"prologue": 0, "direct_tables": 1, "direct": 2, "naive": 3,
            "sep_tables": 4, "gemm": 5, "bwd_direct": 6, "bwd_gemm": 7,
            "bwd_reduce": 8, "batch": 9, "aux": 10, "batch_sep": 11, "recur": 12,
-           "simt": 13}
+           "simt": 13, "bwd_simt": 14}
 
 
 def cgh_kernel_timing(h, enable: bool = True) -> None:

@@ -303,21 +303,17 @@ __device__ __forceinline__ void bwd_store(const BwdPoint &P, const BwdAcc &acc, 
     py[2] = acc.sYY;
 }
 
-// G read from global memory row by row (any alignment, any Nx).
-template <int NPOLY>
-__global__ void __launch_bounds__(BWD_THREADS_GLOBAL)
-direct_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ points,
-                  int N, int Npad, int Nx, int Ny, const float *__restrict__ G,
-                  float *__restrict__ part_x, float *__restrict__ part_y) {
-    static_assert(NPOLY % 2 == 0 && NPOLY <= BWD_STRIP, "polynomial column pairs");
-    const int strip = blockIdx.x;
-    const int j = blockIdx.y * BWD_THREADS_GLOBAL + threadIdx.x;
-    const int x0 = strip * BWD_STRIP;
-    BwdPoint P;
-    BwdAcc acc;
-    bwd_point(rec, points, N, j, x0, P, acc);
+// ------------------------------------------------ walks down a strip
+// G read from global memory row by row (any alignment, any Nx): calls
+// row(y, g) for y = 0 .. Ny-1 with the strip's 16 values as 8 column pairs
+// (zero beyond the frame).
+template <class ROW>
+__device__ __forceinline__ void bwd_global_walk(const float *__restrict__ G, int Nx,
+                                                int Ny, int x0, ROW &&row) {
     const int ncols = Nx - x0 < BWD_STRIP ? Nx - x0 : BWD_STRIP;
-    const bool vec = (ncols == BWD_STRIP) && ((Nx & 3) == 0);
+    // whole 16-byte vectors: a full strip of a 16-byte aligned G whose rows
+    // start 16-byte aligned (Nx a multiple of 4)
+    const bool vec = (ncols == BWD_STRIP) && ((Nx & 3) == 0) && (((uintptr_t)G & 15) == 0);
 #pragma unroll 1
     for (int y = 0; y < Ny; ++y) {
         const float *grow = G + (size_t)y * Nx + x0;
@@ -335,33 +331,25 @@ direct_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ po
                 g[k] = make_float2(2 * k < ncols ? __ldg(grow + 2 * k) : 0.0f,
                                    2 * k + 1 < ncols ? __ldg(grow + 2 * k + 1) : 0.0f);
         }
-        bwd_row<NPOLY>(P, y, g, acc);
+        row(y, g);
     }
-    bwd_store<NPOLY>(P, acc, strip, j, Npad, part_x, part_y);
 }
 
 // G staged through shared memory: the CTA's 16-column strip arrives BWD_RB
 // rows at a time by 2-D TMA loads (zero fill beyond the frame), BWD_NST
-// stages in flight, so the row loads no longer wait on L2 in the loop.  The
+// stages in flight, so the row loads do not wait on L2 in the loop.  The
 // rows are read from shared memory by every thread at the same address
-// (broadcast).  Waits are bounded; a timeout records DEV_TIMEOUT, lets the
-// CTA's own copies land and skips the store.  Needs G 16-byte aligned and Nx
-// a multiple of 4.
-template <int NPOLY>
-__global__ void __launch_bounds__(BWD_THREADS_STAGED)
-direct_bwd_staged_kernel(const __grid_constant__ CUtensorMap tG,
-                         const PointRec *__restrict__ rec,
-                         const float *__restrict__ points, int N, int Npad, int Ny,
-                         float *__restrict__ part_x, float *__restrict__ part_y,
-                         unsigned *status) {
-    static_assert(NPOLY % 2 == 0 && NPOLY <= BWD_STRIP, "polynomial column pairs");
+// (broadcast).  Calls row(y, g) for y = 0 .. Ny-1.  Waits are bounded; after
+// a timeout (DEV_TIMEOUT recorded) the CTA's own copies are let land and the
+// walk returns false.  Needs G 16-byte aligned and Nx a multiple of 4; every
+// thread of the CTA must call it.
+template <class ROW>
+__device__ __forceinline__ bool bwd_staged_walk(const CUtensorMap &tG, int Ny, int x0,
+                                                unsigned *status, ROW &&row) {
     constexpr uint32_t STAGE_BYTES = BWD_RB * BWD_STRIP * sizeof(float);
     __shared__ __align__(128) float sgrow[BWD_NST][BWD_RB][BWD_STRIP];
     __shared__ __align__(8) uint64_t full[BWD_NST];
     __shared__ volatile int abort_flag;
-    const int strip = blockIdx.x;
-    const int j = blockIdx.y * BWD_THREADS_STAGED + threadIdx.x;
-    const int x0 = strip * BWD_STRIP;
     const int nstage = (Ny + BWD_RB - 1) / BWD_RB;
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -377,9 +365,6 @@ direct_bwd_staged_kernel(const __grid_constant__ CUtensorMap tG,
             umma::tma_load_2d(&sgrow[s][0][0], &tG, x0, s * BWD_RB, &full[s]);
             ++issued;
         }
-    BwdPoint P;
-    BwdAcc acc;
-    bwd_point(rec, points, N, j, x0, P, acc);
     int t = 0;
     for (; t < nstage; ++t) {
         const int s = t % BWD_NST;
@@ -399,7 +384,7 @@ direct_bwd_staged_kernel(const __grid_constant__ CUtensorMap tG,
                     g[k] = make_float2(v.x, v.y);
                     g[k + 1] = make_float2(v.z, v.w);
                 }
-                bwd_row<NPOLY>(P, y0 + r, g, acc);
+                row(y0 + r, g);
             }
         }
         __syncthreads();  // every thread is done with slot s
@@ -415,9 +400,183 @@ direct_bwd_staged_kernel(const __grid_constant__ CUtensorMap tG,
         if (threadIdx.x == 0)
             for (int u = t; u < issued; ++u)
                 mbar_wait_bounded(&full[u % BWD_NST], (uint32_t)((u / BWD_NST) & 1));
-        return;
+        return false;
     }
+    return true;
+}
+
+// --------------------------------------------------- direct adjoint
+template <int NPOLY>
+__global__ void __launch_bounds__(BWD_THREADS_GLOBAL)
+direct_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ points,
+                  int N, int Npad, int Nx, int Ny, const float *__restrict__ G,
+                  float *__restrict__ part_x, float *__restrict__ part_y) {
+    static_assert(NPOLY % 2 == 0 && NPOLY <= BWD_STRIP, "polynomial column pairs");
+    const int strip = blockIdx.x;
+    const int j = blockIdx.y * BWD_THREADS_GLOBAL + threadIdx.x;
+    const int x0 = strip * BWD_STRIP;
+    BwdPoint P;
+    BwdAcc acc;
+    bwd_point(rec, points, N, j, x0, P, acc);
+    bwd_global_walk(G, Nx, Ny, x0, [&](int y, const float2 (&g)[BWD_NP2]) {
+        bwd_row<NPOLY>(P, y, g, acc);
+    });
     bwd_store<NPOLY>(P, acc, strip, j, Npad, part_x, part_y);
+}
+
+template <int NPOLY>
+__global__ void __launch_bounds__(BWD_THREADS_STAGED)
+direct_bwd_staged_kernel(const __grid_constant__ CUtensorMap tG,
+                         const PointRec *__restrict__ rec,
+                         const float *__restrict__ points, int N, int Npad, int Ny,
+                         float *__restrict__ part_x, float *__restrict__ part_y,
+                         unsigned *status) {
+    static_assert(NPOLY % 2 == 0 && NPOLY <= BWD_STRIP, "polynomial column pairs");
+    const int strip = blockIdx.x;
+    const int j = blockIdx.y * BWD_THREADS_STAGED + threadIdx.x;
+    const int x0 = strip * BWD_STRIP;
+    BwdPoint P;
+    BwdAcc acc;
+    bwd_point(rec, points, N, j, x0, P, acc);
+    if (bwd_staged_walk(tG, Ny, x0, status, [&](int y, const float2 (&g)[BWD_NP2]) {
+            bwd_row<NPOLY>(P, y, g, acc);
+        }))
+        bwd_store<NPOLY>(P, acc, strip, j, Npad, part_x, part_y);
+}
+
+// ------------------------------------ FP32 separable adjoint (angle addition)
+// The same sums with cos and sin of theta_x + theta_y expanded by angle
+// addition: with (cx, sx) of each column's angle and (cy, sy) of each row's,
+//     sum_y G cos(phi) = cx U - sx V,   sum_y G sin(phi) = sx U + cx V,
+//     U = sum_y G cy,   V = sum_y G sy           (per column, down the strip)
+//     sum_x G sin(phi) = cy P + sy Q,
+//     P = sum_x G sx,   Q = sum_x G cx           (per row, across the strip)
+// Per update: 4 FP32 multiply-adds (U, V, P, Q) and no MUFU operation; the
+// row's sincos (2 MUFU) and the column's (once per strip) are shared by 16
+// updates.  FP32 throughout, like the FP32 separable forward.
+struct Sep32Point {
+    float2 cx[BWD_NP2], sx[BWD_NP2];
+    uint64_t th, dth, d2;
+    float xj, yj;
+    bool valid;
+};
+
+struct Sep32Acc {
+    float2 U[BWD_NP2], V[BWD_NP2];
+    float sY, sYY;
+};
+
+__device__ __forceinline__ void sep32_point(const PointRec *__restrict__ rec,
+                                            const float *__restrict__ points, int N,
+                                            int j, int x0, Sep32Point &P, Sep32Acc &acc) {
+    P.valid = j < N;
+    PointRec pr{};
+    P.xj = 0.0f;
+    P.yj = 0.0f;
+    if (P.valid) {
+        pr = rec[j];
+        P.xj = points[2 * j];
+        P.yj = points[2 * j + 1];
+    }
+    const float2 z2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < BWD_NP2; ++k) {
+        const float a0 =
+            (float)phase_hi(axis_phase(pr.c, pr.bx, pr.ax, x0 + 2 * k)) * RAD_PER_U32;
+        const float a1 =
+            (float)phase_hi(axis_phase(pr.c, pr.bx, pr.ax, x0 + 2 * k + 1)) * RAD_PER_U32;
+        __sincosf(a0, &P.sx[k].x, &P.cx[k].x);
+        __sincosf(a1, &P.sx[k].y, &P.cx[k].y);
+        acc.U[k] = acc.V[k] = z2;
+    }
+    // y angle by the fixed-point recurrence (as bwd_point)
+    P.th = pr.ay;
+    P.dth = pr.c - pr.by;
+    P.d2 = 2 * pr.c;
+    acc.sY = acc.sYY = 0.0f;
+}
+
+__device__ __forceinline__ void sep32_row(Sep32Point &P, int y, const float2 (&g)[BWD_NP2],
+                                          Sep32Acc &acc) {
+    const float ty = (float)phase_hi(P.th) * RAD_PER_U32;
+    P.th += P.dth;
+    P.dth += P.d2;
+    float sy, cy;
+    __sincosf(ty, &sy, &cy);
+    const float dy = (float)y - P.yj;
+    const float2 cy2 = make_float2(cy, cy), sy2 = make_float2(sy, sy);
+    float2 p2 = make_float2(0.0f, 0.0f), q2 = p2;
+#pragma unroll
+    for (int k = 0; k < BWD_NP2; ++k) {
+        acc.U[k] = __ffma2_rn(g[k], cy2, acc.U[k]);
+        acc.V[k] = __ffma2_rn(g[k], sy2, acc.V[k]);
+        p2 = __ffma2_rn(g[k], P.sx[k], p2);
+        q2 = __ffma2_rn(g[k], P.cx[k], q2);
+    }
+    const float r = fmaf(cy, p2.x + p2.y, sy * (q2.x + q2.y));
+    acc.sY = fmaf(r, dy, acc.sY);
+    acc.sYY = fmaf(r * dy, dy, acc.sYY);
+}
+
+__device__ __forceinline__ void sep32_store(const Sep32Point &P, const Sep32Acc &acc,
+                                            int strip, int j, int Npad,
+                                            float *__restrict__ part_x,
+                                            float *__restrict__ part_y) {
+    if (!P.valid) return;
+    float *px = part_x + ((size_t)strip * Npad + j) * 3;
+    float *py = part_y + ((size_t)strip * Npad + j) * 3;
+    const int x0 = strip * BWD_STRIP;
+    float C = 0.0f, sX = 0.0f, sXX = 0.0f;
+#pragma unroll
+    for (int k = 0; k < BWD_NP2; ++k) {
+        const float2 cx = P.cx[k], sx = P.sx[k], U = acc.U[k], V = acc.V[k];
+        C += fmaf(cx.x, U.x, -sx.x * V.x) + fmaf(cx.y, U.y, -sx.y * V.y);
+        const float s0 = fmaf(sx.x, U.x, cx.x * V.x), s1 = fmaf(sx.y, U.y, cx.y * V.y);
+        const float dx0 = (float)(x0 + 2 * k) - P.xj, dx1 = (float)(x0 + 2 * k + 1) - P.xj;
+        const float t0 = s0 * dx0, t1 = s1 * dx1;
+        sX += t0 + t1;
+        sXX = fmaf(t0, dx0, fmaf(t1, dx1, sXX));
+    }
+    px[0] = C;
+    px[1] = sX;
+    px[2] = sXX;
+    py[0] = 0.0f;
+    py[1] = acc.sY;
+    py[2] = acc.sYY;
+}
+
+__global__ void __launch_bounds__(BWD_THREADS_GLOBAL)
+sep32_bwd_kernel(const PointRec *__restrict__ rec, const float *__restrict__ points,
+                 int N, int Npad, int Nx, int Ny, const float *__restrict__ G,
+                 float *__restrict__ part_x, float *__restrict__ part_y) {
+    const int strip = blockIdx.x;
+    const int j = blockIdx.y * BWD_THREADS_GLOBAL + threadIdx.x;
+    const int x0 = strip * BWD_STRIP;
+    Sep32Point P;
+    Sep32Acc acc;
+    sep32_point(rec, points, N, j, x0, P, acc);
+    bwd_global_walk(G, Nx, Ny, x0, [&](int y, const float2 (&g)[BWD_NP2]) {
+        sep32_row(P, y, g, acc);
+    });
+    sep32_store(P, acc, strip, j, Npad, part_x, part_y);
+}
+
+__global__ void __launch_bounds__(BWD_THREADS_STAGED)
+sep32_bwd_staged_kernel(const __grid_constant__ CUtensorMap tG,
+                        const PointRec *__restrict__ rec,
+                        const float *__restrict__ points, int N, int Npad, int Ny,
+                        float *__restrict__ part_x, float *__restrict__ part_y,
+                        unsigned *status) {
+    const int strip = blockIdx.x;
+    const int j = blockIdx.y * BWD_THREADS_STAGED + threadIdx.x;
+    const int x0 = strip * BWD_STRIP;
+    Sep32Point P;
+    Sep32Acc acc;
+    sep32_point(rec, points, N, j, x0, P, acc);
+    if (bwd_staged_walk(tG, Ny, x0, status, [&](int y, const float2 (&g)[BWD_NP2]) {
+            sep32_row(P, y, g, acc);
+        }))
+        sep32_store(P, acc, strip, j, Npad, part_x, part_y);
 }
 
 // ------------------------------------------------------------ reduce
@@ -463,6 +622,7 @@ static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
                                int Nx, int Ny, const float *G, float *gpts,
                                float *gA, float *gz, int method, cudaStream_t s) {
     const bool sep = method == CGH_SEP_FP16X3;
+    const bool sep32 = method == CGH_SEP_FP32;  // strip kernels like the direct one
     const int Kp = pad_to(2 * N, 128);   // GEMM rows: whole 128-row tiles
     const int Npad = sep ? Kp / 2 : pad_to(N, BWD_PAD);
     const int ldx = pad_to(Nx, 8), ldy = pad_to(Ny, 8);
@@ -501,7 +661,7 @@ static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
         tl.done();
     }
     if (!sep) {
-        TimedLaunch tl(h, CGH_K_BWD_DIRECT, s);
+        TimedLaunch tl(h, sep32 ? CGH_K_BWD_SIMT : CGH_K_BWD_DIRECT, s);
         const dim3 grid_st(Tx, Npad / BWD_THREADS_STAGED);
         const dim3 grid_gl(Tx, Npad / BWD_THREADS_GLOBAL);
         // G through shared memory by TMA when its layout allows (16-byte
@@ -509,7 +669,13 @@ static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
         CUtensorMap tG;
         const bool staged = h->bwd_staged && (((uintptr_t)G & 15) == 0) && (Nx % 4 == 0) &&
                             make_f32_map(&tG, G, Nx, Ny, Nx, BWD_STRIP, BWD_RB);
-        if (staged) {
+        if (sep32 && staged) {
+            sep32_bwd_staged_kernel<<<grid_st, BWD_THREADS_STAGED, 0, s>>>(
+                tG, rec, points, N, Npad, Ny, part_x, part_y, h->d_status);
+        } else if (sep32) {
+            sep32_bwd_kernel<<<grid_gl, BWD_THREADS_GLOBAL, 0, s>>>(rec, points, N, Npad, Nx,
+                                                                   Ny, G, part_x, part_y);
+        } else if (staged) {
             if (h->bwd_poly == 0)
                 direct_bwd_staged_kernel<0><<<grid_st, BWD_THREADS_STAGED, 0, s>>>(
                     tG, rec, points, N, Npad, Ny, part_x, part_y, h->d_status);
@@ -627,9 +793,10 @@ extern "C" cgh_status cgh_backward(cgh_handle h, const float *points,
     if (prev != h->device) cudaSetDevice(h->device);
     h->err[0] = 0;
     cgh_status st = h->check_problem(points, A, z, N, lambda, p, Nx, Ny, grad_out);
-    if (st == CGH_OK && method != CGH_DIRECT_FP32 && method != CGH_SEP_FP16X3)
+    if (st == CGH_OK && method != CGH_DIRECT_FP32 && method != CGH_SEP_FP16X3 &&
+        method != CGH_SEP_FP32)
         st = h->fail(CGH_ERR_INVALID_ARG,
-                     "adjoint method must be CGH_DIRECT_FP32 or CGH_SEP_FP16X3");
+                     "adjoint method must be CGH_DIRECT_FP32, CGH_SEP_FP32 or CGH_SEP_FP16X3");
     if (st == CGH_OK &&
         ((((uintptr_t)grad_points) | ((uintptr_t)grad_A) | ((uintptr_t)grad_z)) & 3))
         st = h->fail(CGH_ERR_INVALID_ARG, "gradient arrays must be 4-byte aligned");
