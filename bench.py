@@ -4,9 +4,9 @@
 Workload: the paper's Table 1 frame -- 1920 x 1024 pixels from N = 1024
 object points (integer coordinates, z ~ U[0.5, 1.5] m, lambda = 633 nm,
 p = 6.4 um, seed 0).  One step computes that hologram once by every GPU
-method the build has, in the order: direct FP32 (per-point prologue,
-per-axis angle tables, direct point loop) and separable split-FP16 (U/V
-tables, tcgen05 GEMM).  value = point-pixel updates of all holograms of a
+method the build has, in the order: direct FP32 (per-axis angle tables,
+whose kernel also builds the point records, then the direct point loop) and
+separable split-FP16 (per-point prologue, U/V tables, tcgen05 GEMM).  value = point-pixel updates of all holograms of a
 step, summed over ranks, / step time; the per-method times are in "methods".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]

@@ -1,0 +1,49 @@
+"""Host-side arithmetic of bench.py: the ALU rooflines it reports are the
+best point of the two pipe limits of each kernel's recipe (FMA pipe: 128
+FP32 operations per SM per clock; MUFU: 16 per SM per clock), found here by
+a brute-force scan over the share s of updates on the FMA-pipe polynomial."""
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def _best(fma_ops, mufu_ops, f=128.0, m=16.0):
+    """max over s of min(FMA-pipe limit, MUFU limit) in updates/clk/SM."""
+    s = np.linspace(0.0, 1.0, 200001)
+    fma = f / fma_ops(s)
+    with np.errstate(divide="ignore"):
+        mufu = np.where(mufu_ops(s) > 0, m / np.maximum(mufu_ops(s), 1e-300), np.inf)
+    return float(np.max(np.minimum(fma, mufu)))
+
+
+def test_direct_forward_recipe():
+    # MUFU path 3 FP32 ops + 1 MUFU, polynomial path 9 FP32 ops
+    best = _best(lambda s: 3 * (1 - s) + 9 * s, lambda s: 1 - s)
+    assert abs(best - bench.MIXED_PP_PER_CLK_PER_SM) < 1e-3
+    assert abs(best - 24.89) < 0.01
+
+
+def test_direct_adjoint_recipe():
+    # hardware path 5 FP32 ops + 2 MUFU, polynomial path 17 FP32 ops
+    best = _best(lambda s: 5 * (1 - s) + 17 * s, lambda s: 2 * (1 - s))
+    assert abs(best - bench.ADJ_MIXED_PP_PER_CLK_PER_SM) < 1e-3
+
+
+def test_measured_rate_forms_match_the_recipes():
+    """The closed forms bench.py uses with measured pipe rates f, m are the
+    same scans with f and m in place of 128 and 16."""
+    f, m = 107.0, 15.97
+    fwd = _best(lambda s: 3 * (1 - s) + 9 * s, lambda s: 1 - s, f, m)
+    adj = _best(lambda s: 5 * (1 - s) + 17 * s, lambda s: 2 * (1 - s), f, m)
+    assert abs(fwd - (f + 6 * m) / 9) < 1e-3
+    assert abs(adj - (f + 6 * m) / 17) < 1e-3
+
+
+def test_fma_only_recipes():
+    assert bench.SIMT_PP_PER_CLK_PER_SM == 128 / 2
+    assert bench.BWD_SIMT_PP_PER_CLK_PER_SM == 128 / 4
+    assert bench.RECUR_PP_PER_CLK_PER_SM == 16
