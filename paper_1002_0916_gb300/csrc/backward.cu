@@ -580,25 +580,50 @@ sep32_bwd_staged_kernel(const __grid_constant__ CUtensorMap tG,
 }
 
 // ------------------------------------------------------------ reduce
-__global__ void adjoint_reduce_kernel(const PointRec *__restrict__ rec,
-                                      const float *__restrict__ z, int N, int Npad,
-                                      const float *__restrict__ part_x, int Tx,
-                                      const float *__restrict__ part_y, int Ty,
-                                      const unsigned *gword, float *gpts, float *gA,
-                                      float *gz) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
+// One block per RD_PTS points; its RD_SL slices of threads take every
+// RD_SL-th partial-sum tile of their point (FP64), then slice 0 adds the
+// slices' sums in slice order: deterministic, and enough threads in flight
+// to cover the loads' latency (one thread per point walking ~100 tiles
+// left the SMs nearly empty).
+constexpr int RD_PTS = 32, RD_SL = 8;
+
+__global__ void __launch_bounds__(RD_PTS * RD_SL)
+adjoint_reduce_kernel(const PointRec *__restrict__ rec, const float *__restrict__ z,
+                      int N, int Npad, const float *__restrict__ part_x, int Tx,
+                      const float *__restrict__ part_y, int Ty, const unsigned *gword,
+                      float *gpts, float *gA, float *gz) {
+    __shared__ double part[RD_SL][5][RD_PTS];
+    const int lj = threadIdx.x % RD_PTS, sl = threadIdx.x / RD_PTS;
+    const int j = blockIdx.x * RD_PTS + lj;
     double sC = 0, sX = 0, sXX = 0, sY = 0, sYY = 0;
-    for (int t = 0; t < Tx; ++t) {
-        const float *p = part_x + ((size_t)t * Npad + j) * 3;
-        sC += p[0];
-        sX += p[1];
-        sXX += p[2];
+    if (j < N) {
+        for (int t = sl; t < Tx; t += RD_SL) {
+            const float *p = part_x + ((size_t)t * Npad + j) * 3;
+            sC += p[0];
+            sX += p[1];
+            sXX += p[2];
+        }
+        for (int t = sl; t < Ty; t += RD_SL) {
+            const float *p = part_y + ((size_t)t * Npad + j) * 3;
+            sY += p[1];
+            sYY += p[2];
+        }
     }
-    for (int t = 0; t < Ty; ++t) {
-        const float *p = part_y + ((size_t)t * Npad + j) * 3;
-        sY += p[1];
-        sYY += p[2];
+    part[sl][0][lj] = sC;
+    part[sl][1][lj] = sX;
+    part[sl][2][lj] = sXX;
+    part[sl][3][lj] = sY;
+    part[sl][4][lj] = sYY;
+    __syncthreads();
+    if (sl != 0 || j >= N) return;
+    sC = sX = sXX = sY = sYY = 0;
+#pragma unroll
+    for (int q = 0; q < RD_SL; ++q) {
+        sC += part[q][0][lj];
+        sX += part[q][1][lj];
+        sXX += part[q][2][lj];
+        sY += part[q][3][lj];
+        sYY += part[q][4][lj];
     }
     const PointRec r = rec[j];
     const bool ok = r.Q32 > 0.0f;
@@ -770,7 +795,7 @@ static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
     }
     {
         TimedLaunch tl(h, CGH_K_BWD_REDUCE, s);
-        adjoint_reduce_kernel<<<(N + 127) / 128, 128, 0, s>>>(
+        adjoint_reduce_kernel<<<(N + RD_PTS - 1) / RD_PTS, RD_PTS * RD_SL, 0, s>>>(
             rec, z, N, Npad, part_x, Tx, part_y, Ty, sep ? gword : nullptr, gpts, gA,
             gz);
         cudaError_t e = cudaGetLastError();
