@@ -160,15 +160,16 @@ __global__ void adj_tables_kernel(const PointRec *__restrict__ rec, int N,
 // sign is restored at the end.
 constexpr int BWD_STRIP = 16;    // pixels per column strip
 // points per CTA: 256 with G staged through shared memory (each staged row
-// serves more points), 128 reading G rows from global memory (measured:
-// 3.34 against 3.44 ms staged, 3.59 against 4.10 ms unstaged at
-// 1920x1080x4096); points are padded to the larger
+// serves more points), 128 reading G rows from global memory (measured on
+// the direct adjoint at 1920x1080x4096, before the per-column sums: 3.34
+// against 3.44 ms staged, 3.59 against 4.10 ms unstaged); points are padded
+// to the larger
 constexpr int BWD_THREADS_STAGED = 256;
 constexpr int BWD_THREADS_GLOBAL = 128;
 constexpr int BWD_PAD = 256;
 constexpr int BWD_NP2 = BWD_STRIP / 2;
-// G staged through shared memory (direct_bwd_staged_kernel): BWD_RB rows of
-// the CTA's strip per stage, BWD_NST stages in flight
+// G staged through shared memory (bwd_staged_walk): BWD_RB rows of the
+// CTA's strip per stage, BWD_NST stages in flight
 constexpr int BWD_RB = 32;
 constexpr int BWD_NST = 4;
 
