@@ -158,6 +158,20 @@ cgh_status cgh_forward_host_async(cgh_handle h, const float *points_host,
  * CGH_ERR_CUDA if either failed. */
 cgh_status cgh_host_wait(cgh_handle h, void *stream);
 
+/* Tickets, for pipelines that keep more than one call in flight: the
+ * cgh_forward_host_async calls of a handle are numbered 1, 2, ...;
+ * cgh_host_ticket returns the number of the last one (0 before any).
+ * cgh_host_wait_ticket blocks until every call up to and including `ticket`
+ * has finished, its output copy included (their host outputs are then
+ * complete, their inputs free), leaving later calls running.  A ticket that
+ * was already waited for returns at once; one beyond the last call is
+ * CGH_ERR_INVALID_ARG.  The handle remembers the last CGH_HOST_TICKETS calls;
+ * a new call first waits for the call that many before it.  CGH_ERR_CUDA if
+ * the work failed. */
+#define CGH_HOST_TICKETS 16
+uint64_t cgh_host_ticket(cgh_handle h);
+cgh_status cgh_host_wait_ticket(cgh_handle h, uint64_t ticket);
+
 /* Adjoint of Eq. 1.  grad_out: device, Ny*Nx floats, dL/dI for some loss L.
  * Writes (device, N entries each; grad_points N x 2 interleaved):
  *   grad_A[j]          = sum_pix G cos(phi)

@@ -32,7 +32,7 @@ __all__ = [
     "cgh_kernel_timing", "cgh_kernel_time", "cgh_tune_batch",
     "cgh_kernel_timing_mask", "cgh_set_gemm_tiles", "GEMM_TILES",
     "cgh_debug_pipe_rates", "cgh_direct_tile_for", "cgh_forward_host_async",
-    "cgh_host_wait", "cgh_gemm_plan",
+    "cgh_host_wait", "cgh_gemm_plan", "cgh_host_ticket", "cgh_host_wait_ticket",
 ]
 
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
@@ -83,6 +83,10 @@ def _load():
     L.cgh_forward_host.argtypes = L.cgh_forward.argtypes
     L.cgh_forward_host_async.argtypes = L.cgh_forward.argtypes
     L.cgh_host_wait.argtypes = [vp, vp]
+    L.cgh_host_ticket.argtypes = [vp]
+    L.cgh_host_ticket.restype = ctypes.c_uint64
+    L.cgh_host_wait_ticket.argtypes = [vp, ctypes.c_uint64]
+    L.cgh_host_wait_ticket.restype = ci
     L.cgh_backward.argtypes = [vp, fp, fp, fp, ci, cd, cd, ci, ci, fp, fp, fp,
                                fp, ci, vp]
     L.cgh_batch.argtypes = [vp, ctypes.POINTER(_Problem), ci, ci, vp]
@@ -282,6 +286,17 @@ def cgh_host_wait(handle, stream=None):
     """Wait for ``stream`` and for the host copies of earlier
     ``cgh_forward_host_async`` calls of ``handle``."""
     _check(handle, _L().cgh_host_wait(handle, _stream_ptr(stream)), "cgh_host_wait")
+
+
+def cgh_host_ticket(handle) -> int:
+    """Number of the last ``cgh_forward_host_async`` call of ``handle``."""
+    return int(_L().cgh_host_ticket(handle))
+
+
+def cgh_host_wait_ticket(handle, ticket: int) -> None:
+    """Wait until every asynchronous host call up to ``ticket`` has finished
+    (outputs complete, inputs free), leaving later calls running."""
+    _check(handle, _L().cgh_host_wait_ticket(handle, int(ticket)), "cgh_host_wait_ticket")
 
 
 # ------------------------------------------------------------ backward

@@ -276,6 +276,11 @@ void cgh_ctx::release_all() {
     }
     if (copy_stream) cudaStreamDestroy(copy_stream);
     copy_stream = nullptr;
+    for (cudaEvent_t &e : host_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    host_calls = host_done = 0;
 }
 
 // --------------------------------------------------------- kernel timing
@@ -528,10 +533,26 @@ cgh_status cgh_forward_host_async(cgh_handle h, const float *points_host,
                        "cgh_forward_host_async needs page-locked, mapped host buffers");
     const bool progressive = method == CGH_DIRECT_FP32 || method == CGH_NAIVE_FP32 ||
                              method == CGH_RECUR_FP32 || method == CGH_SEP_FP32;
-    if (progressive)
-        return h->forward(m_pts, m_A, m_z, N, lambda, p, Nx, Ny, m_out, method, s);
-
+    // this call's ticket: its event slot must be free (the call that many
+    // tickets back has finished)
+    const uint64_t ticket = h->host_calls + 1;
+    cudaEvent_t &tev = h->host_ev[ticket % CGH_HOST_TICKETS];
+    if (ticket > CGH_HOST_TICKETS && h->host_done < ticket - CGH_HOST_TICKETS) {
+        st = cgh_host_wait_ticket(h, ticket - CGH_HOST_TICKETS);
+        if (st) return st;
+    }
     cudaError_t e = cudaSuccess;
+    if (!tev) e = cudaEventCreateWithFlags(&tev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return h->cuda_fail(e, "ticket event");
+    if (progressive) {
+        st = h->forward(m_pts, m_A, m_z, N, lambda, p, Nx, Ny, m_out, method, s);
+        if (st) return st;
+        e = cudaEventRecord(tev, s);
+        if (e != cudaSuccess) return h->cuda_fail(e, "ticket event");
+        h->host_calls = ticket;
+        return CGH_OK;
+    }
+
     if (!h->copy_stream) {
         e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
@@ -558,9 +579,33 @@ cgh_status cgh_forward_host_async(cgh_handle h, const float *points_host,
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out_host, d_out, out_b, cudaMemcpyDeviceToHost, h->copy_stream);
     if (e == cudaSuccess) e = cudaEventRecord(h->hout_copied[k], h->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(tev, h->copy_stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "device-to-host copy");
     h->hout_pending[k] = true;
     h->hout_next = k ^ 1;
+    h->host_calls = ticket;
+    return CGH_OK;
+}
+
+uint64_t cgh_host_ticket(cgh_handle h) { return h ? h->host_calls : 0; }
+
+cgh_status cgh_host_wait_ticket(cgh_handle h, uint64_t ticket) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    if (ticket > h->host_calls)
+        return h->fail(CGH_ERR_INVALID_ARG, "ticket %llu was not issued (last %llu)",
+                       (unsigned long long)ticket, (unsigned long long)h->host_calls);
+    DeviceGuard g(h->device);
+    // calls finish out of order across the two streams: wait for each
+    // outstanding call up to the ticket (the ring holds the last
+    // CGH_HOST_TICKETS of them, all of which are outstanding or done)
+    uint64_t u = h->host_done + 1;
+    if (ticket > CGH_HOST_TICKETS && u < ticket - CGH_HOST_TICKETS + 1)
+        u = ticket - CGH_HOST_TICKETS + 1;
+    for (; u <= ticket; ++u) {
+        cudaError_t e = cudaEventSynchronize(h->host_ev[u % CGH_HOST_TICKETS]);
+        if (e != cudaSuccess) return h->cuda_fail(e, "cgh_host_wait_ticket");
+    }
+    if (ticket > h->host_done) h->host_done = ticket;
     return CGH_OK;
 }
 
@@ -571,6 +616,7 @@ cgh_status cgh_host_wait(cgh_handle h, void *stream) {
     if (e == cudaSuccess && h->copy_stream) e = cudaStreamSynchronize(h->copy_stream);
     if (e != cudaSuccess) return h->cuda_fail(e, "cgh_host_wait");
     h->hout_pending[0] = h->hout_pending[1] = false;
+    h->host_done = h->host_calls;
     return CGH_OK;
 }
 

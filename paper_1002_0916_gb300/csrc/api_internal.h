@@ -50,6 +50,11 @@ struct cgh_ctx {
     cudaEvent_t hout_ready[2] = {nullptr, nullptr};
     cudaEvent_t hout_copied[2] = {nullptr, nullptr};
     bool hout_pending[2] = {false, false};
+    // tickets of the asynchronous host calls: the number of calls issued and
+    // of calls known finished, and per call (mod CGH_HOST_TICKETS) the event
+    // recorded after its last piece of work
+    uint64_t host_calls = 0, host_done = 0;
+    cudaEvent_t host_ev[CGH_HOST_TICKETS] = {};
 
     // batch: pinned staging of the work list, a private capture stream and
     // the instantiated graph of the last batch geometry

@@ -136,3 +136,64 @@ def test_refused_inside_capture(cg, h):
         finally:
             g.capture_end()   # an empty graph: nothing was enqueued
     assert ei.value.status == cg.CGH_ERR_UNSUPPORTED
+
+
+def test_tickets_pipeline_two_steps_in_flight(cg):
+    """A display-loop pipeline: each step issues a split-FP16 and a direct
+    hologram into its own pair of pinned buffers, then waits only for the
+    previous step's ticket.  Every step's outputs are exact once its ticket
+    has been waited for, although the next step is already running."""
+    hh = cg.cgh_create(0)
+    try:
+        clouds = [make_cloud(400 + k, 200, 256, 160, integer=(k % 2 == 0), zlo=0.3,
+                             zhi=0.9, lam=532e-9, p=8e-6) for k in range(6)]
+        refs = [(_sync(cg, hh, c, "sep_fp16x3"), _sync(cg, hh, c, "direct")) for c in clouds]
+        bufs = [(_out(clouds[0]), _out(clouds[0])) for _ in range(2)]
+        ins = [_host(c) for c in clouds]
+        assert cg.cgh_host_ticket(hh) == 0
+        prev = None
+        for k, c in enumerate(clouds):
+            o = bufs[k % 2]
+            cg.cgh_forward_host_async(*ins[k], c.lam, c.p, c.Nx, c.Ny, out=o[0],
+                                      method="sep_fp16x3", handle=hh)
+            cg.cgh_forward_host_async(*ins[k], c.lam, c.p, c.Nx, c.Ny, out=o[1],
+                                      method="direct", handle=hh)
+            t = cg.cgh_host_ticket(hh)
+            assert t == 2 * (k + 1)
+            if prev is not None:
+                cg.cgh_host_wait_ticket(hh, prev)
+                po = bufs[(k - 1) % 2]
+                assert np.array_equal(po[0].numpy(), refs[k - 1][0])
+                assert np.array_equal(po[1].numpy(), refs[k - 1][1])
+            prev = t
+        cg.cgh_host_wait_ticket(hh, prev)
+        o = bufs[(len(clouds) - 1) % 2]
+        assert np.array_equal(o[0].numpy(), refs[-1][0])
+        assert np.array_equal(o[1].numpy(), refs[-1][1])
+        cg.cgh_host_wait_ticket(hh, 3)          # long done: returns at once
+        with pytest.raises(cg.CGHError) as ei:
+            cg.cgh_host_wait_ticket(hh, prev + 1)
+        assert ei.value.status == cg.CGH_ERR_INVALID_ARG
+    finally:
+        cg.cgh_destroy(hh)
+
+
+def test_tickets_beyond_the_ring(cg):
+    """More calls in flight than the handle remembers: a new call first
+    waits for the one CGH_HOST_TICKETS before it, and every output is
+    right."""
+    hh = cg.cgh_create(0)
+    try:
+        c = make_cloud(450, 120, 128, 96, integer=True, zlo=0.3, zhi=0.9,
+                       lam=633e-9, p=6.4e-6)
+        ref = _sync(cg, hh, c, "sep_fp16x3")
+        ins = _host(c)
+        outs = [_out(c) for _ in range(40)]
+        for o in outs:
+            cg.cgh_forward_host_async(*ins, c.lam, c.p, c.Nx, c.Ny, out=o,
+                                      method="sep_fp16x3", handle=hh)
+        cg.cgh_host_wait_ticket(hh, cg.cgh_host_ticket(hh))
+        for o in outs:
+            assert np.array_equal(o.numpy(), ref)
+    finally:
+        cg.cgh_destroy(hh)
