@@ -142,9 +142,10 @@ cgh_status cgh_forward_host(cgh_handle h, const float *points_host,
  * tensor-core methods compute into one of two device buffers of the handle
  * (used in turn) and copy it to out_host on a copy stream of the handle, so
  * that the copy runs while the next call's kernels do.  A call waits on the
- * device (not the host) for the copy out of its buffer two calls earlier.
- * The inputs must stay unchanged, and out_host unread, until
- * cgh_host_wait returns.  Not inside stream capture
+ * device (not the host) for the copy out of its buffer two tensor-core
+ * calls earlier.  The inputs must stay unchanged, and out_host unread, until
+ * cgh_host_wait (or cgh_host_wait_ticket for this call) returns.  Not
+ * inside stream capture
  * (CGH_ERR_UNSUPPORTED).  Results are bit for bit those of
  * cgh_forward_host.  Other errors as cgh_forward. */
 cgh_status cgh_forward_host_async(cgh_handle h, const float *points_host,
