@@ -76,7 +76,7 @@ def main():
     print("| adjoint (1920x1080x4096, 64 sampled points) | rel err A | x | y | z |")
     print("|---|---|---|---|---|")
     Gd = torch.from_numpy(G).cuda()
-    for m in ("direct", "sep_fp16x3"):
+    for m in ("direct", "sep_fp32", "sep_fp16x3"):
         gp, gA, gz = cg.cgh_backward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, Gd,
                                      method=m, handle=h)
         torch.cuda.synchronize()
