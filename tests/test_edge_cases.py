@@ -1,8 +1,10 @@
 """Edge cases of the point cloud for every forward method, against the FP64
 oracle through the C ABI: the maximum point count (N = 2^24) and one past
-it, and degenerate clouds (coincident points, points exactly on pixels,
+it, degenerate clouds (coincident points, points exactly on pixels,
 near-zero phase from a very distant point, zero and negative amplitudes,
-points far outside the frame).
+points far outside the frame), points up to 3e6 pixels away with signed
+amplitudes and a point near the records' Fresnel limit (forward and
+adjoint).
 Bounds: FP32 paths max |I - I_ref| <= 1e-4 sum|A_j|; split FP16 relative
 RMS <= 1e-4 (or, where I_ref is near zero, max error <= 1e-4 sum|A_j|)."""
 import numpy as np
@@ -282,3 +284,47 @@ def test_coherent_sum_single_pass(cg, h, oracle_mod, method):
     got = _fwd(cg, h, c, method)
     assert cg.cgh_launch_count(h) - n0 == 2 + 2  # prologue, tables, 2 chunks
     assert rel_rms(got, oracle_mod.forward(c)) <= 1e-2
+
+
+def _far_and_signed_cloud(seed, Nx, Ny):
+    """Random points with signed amplitudes, plus points up to 3e6 pixels
+    outside the frame and one point close to the Fresnel limit of the
+    records (Q = p^2 / (2 lambda z) = 0.9 turn per pixel^2: a fringe pattern
+    aliased far past the Nyquist rate, still defined pixel by pixel)."""
+    rng = np.random.default_rng(seed)
+    lam, p = 532e-9, 8e-6
+    n = 60
+    xy = np.stack([rng.uniform(0, Nx, n), rng.uniform(0, Ny, n)], 1).tolist()
+    A = rng.uniform(-1.0, 1.0, n).tolist()
+    z = rng.uniform(0.2, 1.0, n).tolist()
+    for (x, y) in [(1.0e5, 10.0), (-1.0e5, -2.5e4), (3.0e6, Ny / 2), (Nx / 2, -3.0e6)]:
+        xy.append((x, y)); A.append(float(rng.uniform(-1, 1))); z.append(0.7)
+    xy.append((Nx / 3, Ny / 4)); A.append(0.6); z.append(p * p / (2 * lam * 0.9))
+    return Cloud(xy=np.array(xy, np.float32), A=np.array(A, np.float32),
+                 z=np.array(z, np.float32), lam=lam, p=p, Nx=Nx, Ny=Ny,
+                 name="far_and_signed")
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_far_points_signed_amplitudes_near_fresnel_limit(cg, h, oracle_mod, method):
+    c = _far_and_signed_cloud(31, 96, 70)
+    _check(c, _fwd(cg, h, c, method), oracle_mod.forward(c), method)
+
+
+@pytest.mark.parametrize("method", ["direct", "sep_fp32", "sep_fp16x3"])
+def test_adjoint_far_points_signed_amplitudes(cg, h, oracle_mod, method):
+    """The adjoint of the same cloud: every parameter group within 1e-3 of
+    the FP64 gradient, the far points' large offsets included."""
+    import torch
+    from workloads import grad_field
+    c = _far_and_signed_cloud(32, 96, 70)
+    G = grad_field(33, c.Nx, c.Ny)
+    pts, A, z = to_dev(c)
+    gp, gA, gz = cg.cgh_backward(pts, A, z, c.lam, c.p, c.Nx, c.Ny,
+                                 torch.from_numpy(G).cuda(), method=method, handle=h)
+    torch.cuda.synchronize()
+    assert cg.cgh_last_device_status(h) == cg.CGH_OK
+    rp, rA, rz = oracle_mod.grad(c, G.astype(np.float64))
+    for got, want in ((gA, rA), (gp[:, 0], rp[:, 0]), (gp[:, 1], rp[:, 1]), (gz, rz)):
+        g64 = got.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(g64 - want) <= 1e-3 * np.linalg.norm(want), method
