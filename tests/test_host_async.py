@@ -197,3 +197,22 @@ def test_tickets_beyond_the_ring(cg):
             assert np.array_equal(o.numpy(), ref)
     finally:
         cg.cgh_destroy(hh)
+
+
+@pytest.mark.parametrize("method", ["direct", "sep_fp16x3"])
+def test_async_empty_cloud_gives_zeros(cg, h, method):
+    """N = 0 through the asynchronous call: the hologram is all zeros and the
+    call takes a ticket like any other."""
+    import torch
+    from workloads import Cloud
+    c = Cloud(xy=np.zeros((0, 2), np.float32), A=np.zeros(0, np.float32),
+              z=np.zeros(0, np.float32), lam=532e-9, p=8e-6, Nx=70, Ny=40, name="empty")
+    ins = [torch.zeros(0).pin_memory() for _ in range(3)]
+    ins[0] = torch.zeros((0, 2)).pin_memory()
+    out = _out(c)
+    t0 = cg.cgh_host_ticket(h)
+    cg.cgh_forward_host_async(*ins, c.lam, c.p, c.Nx, c.Ny, out=out, method=method,
+                              handle=h)
+    assert cg.cgh_host_ticket(h) == t0 + 1
+    cg.cgh_host_wait_ticket(h, t0 + 1)
+    assert np.all(out.numpy() == 0.0)
