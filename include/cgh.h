@@ -102,11 +102,17 @@ typedef enum {
 
 /* Create a handle bound to CUDA device `device` (made current on the calling
  * thread).  *out receives the handle.  Errors: CGH_ERR_INVALID_ARG (out NULL,
- * bad device), CGH_ERR_CUDA. */
+ * bad device), CGH_ERR_CUDA.
+ * Paper: host steps (1) and (2) of Section 2 (initialise the GPU, allocate
+ * device memory).  Here the handle records the device and its SM count and
+ * allocates the device status word; the workspace of step (2) is allocated
+ * later, on the first call of each shape, and kept. */
 cgh_status cgh_create(cgh_handle *out, int device);
 
 /* Free the handle and its workspace.  Synchronises the device first.
- * NULL is accepted and ignored. */
+ * NULL is accepted and ignored.
+ * Paper: host step (6) of Section 2 (release the device memory and the GPU
+ * resources). */
 cgh_status cgh_destroy(cgh_handle h);
 
 /* Eq. 1 for one hologram.  points, A, z: device, N points (N >= 0; N = 0
@@ -208,7 +214,10 @@ typedef struct {
 } cgh_problem;
 
 /* Many holograms of uneven size, N and wavelength in one persistent launch
- * (after one prologue launch).  probs: host array of `count` problems
+ * (after one prologue launch).  Each problem is one evaluation of Eq. 1
+ * (Section 1) with its own points, constants and frame; the paper's
+ * Table 1 runs the same 1,920 x 1,024 frame once per point count, and this
+ * call runs many such frames (of any size) as one piece of device work.  probs: host array of `count` problems
  * (1 <= count <= 4096).  The work list of (problem, tile) items is built on
  * the host, sorted longest-first, and pulled by the persistent CTAs from an
  * atomic counter.  method: CGH_DIRECT_FP32 or CGH_SEP_FP16X3.
@@ -235,20 +244,28 @@ cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int count,
  * create a cgh_handle, so this call needs none.
  *
  * Computes the same hologram as cgh_forward(..., CGH_DIRECT_FP32, ...) on
- * the calling thread's current device, using the same kernels, but takes
- * all scratch (angle tables, amplitudes, status word) from one fixed
- * __device__ array of CGH_NOALLOC_SCRATCH_BYTES.  It calls no cudaMalloc,
- * cudaFree or other allocating routine.  points, A, z, out: device memory
- * owned by the caller, layouts as cgh_forward; stream: cudaStream_t or NULL.
+ * the calling thread's current device, using the same kernels (the tile
+ * shape cgh_forward's built-in heuristic picks for the frame, and its
+ * default schedule when that schedule's scratch fits), but takes all
+ * scratch (angle tables, amplitudes, the schedule's partial tiles and
+ * counters, status word) from one fixed __device__ array of
+ * CGH_NOALLOC_SCRATCH_BYTES.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.  points, A, z, out: device memory owned by the
+ * caller, layouts as cgh_forward; stream: cudaStream_t or NULL.
  * Asynchronous on `stream`.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and remembers it; make that first call before any
- * stream capture.  Every call on a device shares the array and leaves its
- * contents behind; each call clears what it needs cleared, but calls whose
- * work overlaps on the GPU (other streams, other threads) race on the array
- * and must be serialised by the caller.  Points with z <= 0 or non-finite
- * values are skipped; there is no status read-back in this variant.
+ * The first call in a CUDA context looks up the array's device address
+ * (cudaGetSymbolAddress, with the device current) and remembers it with the
+ * context's id; make that first call before any stream capture.  After
+ * cudaDeviceReset, or when the primary context is released and created
+ * again, the next call is again a first call: it looks the address up anew.
+ * Every call on a device shares the array and leaves its contents behind;
+ * each call clears what it needs cleared, but calls whose work overlaps on
+ * the GPU (other streams, other threads) race on the array and must be
+ * serialised by the caller.  There is no status read-back in this variant:
+ * points with z <= 0 or non-finite values are skipped unreported, and if a
+ * bounded device-side wait ever gave up (see the conventions above), the
+ * tiles of the CTAs concerned would be left unwritten, also unreported.
  *
  * Returns CGH_OK; CGH_ERR_INVALID_ARG for the argument errors cgh_forward
  * rejects; CGH_ERR_UNSUPPORTED when the frame needs more scratch than the
@@ -408,13 +425,20 @@ cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs, int count,
 
 /* Synchronise `stream`, then read and clear the handle's device status
  * word: CGH_OK, CGH_ERR_INVALID_ARG (a point had z <= 0 or a non-finite
- * value), CGH_ERR_TIMEOUT (a bounded wait gave up), CGH_ERR_CUDA. */
+ * value), CGH_ERR_TIMEOUT (a bounded wait gave up), CGH_ERR_CUDA.
+ * Paper: host step (5) of Section 2 (receive the result from the device)
+ * says nothing of errors; this call is the read-back of what only the
+ * device sees.  Eq. 1 needs z_j > 0 (P_j = pi p^2 / (lambda z_j)), so a
+ * point that breaks it is skipped and reported here. */
 cgh_status cgh_last_device_status(cgh_handle h, void *stream);
 
 /* Number of kernels this handle has launched since creation. */
 uint64_t cgh_launch_count(cgh_handle h);
 
-/* Static text for a status code (never NULL). */
+/* Static text for a status code (never NULL).  The paper's host steps
+ * (Section 2, steps (1)-(6)) define no error codes; these are the outcomes
+ * of this library's argument checks and of the CUDA calls behind those
+ * steps. */
 const char *cgh_status_string(int status);
 
 /* Text of the handle's most recent error (never NULL; "" if none). */

@@ -5,7 +5,8 @@ Bound (FP32 paths): max |I - I_ref| <= 1e-4 sum |A_j|."""
 import numpy as np
 import pytest
 
-from gpu_util import max_abs, rel_rms, sample_rows, sum_abs_A, to_dev
+from gpu_util import max_abs, record, rel_rms, sample_rows, sum_abs_A, to_dev
+from oracle_cache import workload_rows
 from workloads import make_cloud, table1_cloud, workload
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +40,7 @@ def _fwd(cg, h, c, method="recur"):
 
 def test_cfg1_full_frame(cg, h, oracle_mod):
     c = workload("cfg1_256x256_n64")
-    err = max_abs(_fwd(cg, h, c), oracle_mod.forward(c))
+    err, _ = record(c.name, "recur", _fwd(cg, h, c), oracle_mod.forward(c), c)
     assert err <= TOL * sum_abs_A(c), err
     assert cg.cgh_last_device_status(h) == cg.CGH_OK
 
@@ -108,17 +109,29 @@ def test_cfg2_paper_frame_sampled_rows(cg, h, oracle_mod):
     c = workload("cfg2_1920x1024_n1024")
     I = _fwd(cg, h, c)
     rows = sample_rows(c.Ny, 24, seed=3)
-    err = max_abs(I[rows], oracle_mod.forward(c, rows=rows))
+    err, _ = record(c.name, "recur", I[rows], oracle_mod.forward(c, rows=rows), c)
     assert err <= TOL * sum_abs_A(c), err
     # the same hologram as the per-axis-table kernel, to rounding
     assert max_abs(I, _fwd(cg, h, c, "direct")) <= 2e-5 * sum_abs_A(c)
+
+
+def test_cfg3_large_frame_sampled_rows(cg, h):
+    """3840 x 2160 pixels, 16384 continuous points: the Eq. 2 recurrence
+    kernel over the full frame, the FP64 oracle (Eq. 1) on 64 evenly spaced
+    rows plus 8 random ones."""
+    c = workload("cfg3_3840x2160_n16384")
+    I = _fwd(cg, h, c)
+    rows, ref = workload_rows(c.name)
+    err, _ = record(c.name, "recur", I[rows], ref, c)
+    assert err <= TOL * sum_abs_A(c), err
+    assert np.all(np.isfinite(I))
 
 
 def test_cfg5_continuous_sampled_rows(cg, h, oracle_mod):
     c = workload("cfg5_1920x1080_n4096")
     I = _fwd(cg, h, c)
     rows = sample_rows(c.Ny, 6, seed=21)
-    err = max_abs(I[rows], oracle_mod.forward(c, rows=rows))
+    err, _ = record(c.name, "recur", I[rows], oracle_mod.forward(c, rows=rows), c)
     assert err <= TOL * sum_abs_A(c), err
 
 
