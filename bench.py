@@ -6,7 +6,8 @@ object points (integer coordinates, z ~ U[0.5, 1.5] m, lambda = 633 nm,
 p = 6.4 um, seed 0).  One step computes that hologram once by every GPU
 method the build has, in the order: direct FP32 (per-axis angle tables,
 whose kernel also builds the point records, then the direct point loop) and
-separable split-FP16 (per-point prologue, U/V tables, tcgen05 GEMM).  value = point-pixel updates of all holograms of a
+separable split-FP16 (U/V tables, whose kernel also builds the point
+records, then the tcgen05 GEMM).  value = point-pixel updates of all holograms of a
 step, summed over ranks, / step time; the per-method times are in "methods".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -90,6 +91,19 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="host time budget of the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--split", choices=["replicas", "rows", "problems"],
+                    default="replicas",
+                    help="several GPUs (torchrun): replicas = every rank its own copy "
+                         "of the workload (weak scaling, the default); rows = each rank "
+                         "a slab of each hologram's rows (paper, large; strong "
+                         "scaling); problems = each rank an LPT share of the batch "
+                         "(batch64; strong scaling).  No collective on the data path.")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the built-in heuristics' shapes instead of running the "
+                         "library's autotuner (cgh_tune, cgh_tune_batch) first")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (large frame, 64-hologram batch, "
+                         "adjoint) that the default line reports under 'extra'")
     ap.add_argument("--methods", default=None,
                     help="comma-separated methods (default: direct,sep_fp16x3; "
                          "table1: direct,recur,sep_fp32,sep_fp16x3)")
@@ -318,6 +332,9 @@ class Leg:
         self.gemm_flops, self.gemm_launches = gemm_flops, gemm_launches
         self.kernel = kernel          # the kernel that does this leg's updates
         self.method, self.N = method or name, N
+        self.problems = None          # batch legs: the problems (for the tuner)
+        self.plan = None              # batch legs: what cgh_batch runs
+        self.size = None              # forward legs: (N, Nx, Ny) of one call
 
 
 # kernel (cgh_kernel_id name) that carries a forward method's point-pixel work
@@ -330,8 +347,11 @@ GEMM_PASSES = {"sep_fp16x3": 3.0, "sep_fp16": 1.0, "sep_bf16": 1.0}
 PROGRESSIVE = {"direct", "naive", "recur", "sep_fp32"}
 
 
-def build_legs(cg, h, which, methods, dev, stream):
-    """The legs of one step of workload `which` (tensors on `dev`)."""
+def build_legs(cg, h, which, methods, dev, stream, shard=None):
+    """The legs of one step of workload `which` (tensors on `dev`).  shard:
+    None (the whole workload), ("rows", y0, rows) (a slab of each hologram's
+    rows, cgh_forward_rows) or ("problems", [indices]) (those problems of
+    the batch)."""
     import torch
 
     from workloads import batch_problems, grad_field, workload
@@ -348,14 +368,31 @@ def build_legs(cg, h, which, methods, dev, stream):
             pts, A, z, c.lam, c.p, c.Nx, c.Ny, out=out, method=m, handle=h,
             stream=stream))
         mult = GEMM_PASSES.get(m, 0.0)
-        return Leg(name, fn, c.pp, 4.0 * c.pp * mult, 1 if mult else 0,
-                   kernel=MAIN_KERNEL.get(m), method=m, N=c.N)
+        leg = Leg(name, fn, c.pp, 4.0 * c.pp * mult, 1 if mult else 0,
+                  kernel=MAIN_KERNEL.get(m), method=m, N=c.N)
+        leg.size = (c.N, c.Nx, c.Ny)
+        return leg
+
+    def slab_leg(c, m, pts, A, z, name, y0, rows):
+        out = torch.empty((max(rows, 1), c.Nx), dtype=torch.float32, device=dev)
+        fn = ((lambda m=m, out=out: cg.cgh_forward_rows(
+            pts, A, z, c.lam, c.p, c.Nx, y0, rows, out=out, method=m, handle=h,
+            stream=stream)) if rows > 0 else (lambda: None))
+        pp = rows * c.Nx * c.N
+        mult = GEMM_PASSES.get(m, 0.0)
+        leg = Leg(name, fn, pp, 4.0 * pp * mult, 1 if mult else 0,
+                  kernel=MAIN_KERNEL.get(m), method=m, N=c.N)
+        leg.size = (c.N, c.Nx, rows) if rows > 0 else None
+        return leg
 
     if which in ("paper", "large"):
         c = workload(WORKLOAD if which == "paper" else "cfg3_3840x2160_n16384")
         pts, A, z = dev_cloud(c)
         for m in methods:
-            legs.append(forward_leg(c, m, pts, A, z, m))
+            if shard is not None and shard[0] == "rows":
+                legs.append(slab_leg(c, m, pts, A, z, m, shard[1], shard[2]))
+            else:
+                legs.append(forward_leg(c, m, pts, A, z, m))
         return c, legs
     if which == "table1":
         from workloads import TABLE1_POINTS, table1_cloud
@@ -367,6 +404,8 @@ def build_legs(cg, h, which, methods, dev, stream):
         return c, legs
     if which == "batch64":
         clouds = batch_problems(seed=0)
+        if shard is not None and shard[0] == "problems":
+            clouds = [clouds[i] for i in shard[1]]
         probs = []
         for cl in clouds:
             p_, A_, z_ = dev_cloud(cl)
@@ -378,10 +417,17 @@ def build_legs(cg, h, which, methods, dev, stream):
         for m in methods:
             if m not in ("direct", "sep_fp16x3"):
                 continue
-            fn = (lambda m=m: cg.cgh_batch(probs, method=m, handle=h, stream=stream))
+            fn = ((lambda m=m: cg.cgh_batch(probs, method=m, handle=h, stream=stream))
+                  if probs else (lambda: None))
+            # the separable batch's timed kernel is its whole graph (prologue,
+            # tables and grouped split-FP16 GEMM): 3 passes of 4 pp flops
             legs.append(Leg("batch_" + m, fn, pp,
+                            12.0 * pp if m == "sep_fp16x3" else 0.0,
+                            1 if m == "sep_fp16x3" else 0,
                             kernel="batch" if m == "direct" else "batch_sep"))
-        return clouds[0], legs
+        for leg in legs:
+            leg.problems = probs
+        return (clouds[0] if clouds else batch_problems(seed=0)[0]), legs
     if which == "adjoint":
         c = workload("cfg5_1920x1080_n4096")
         pts, A, z = dev_cloud(c)
@@ -405,6 +451,247 @@ def build_legs(cg, h, which, methods, dev, stream):
                                 m, "bwd_gemm")))
         return c, legs
     raise SystemExit(f"unknown workload {which}")
+
+
+ALU_KERNELS = ("direct", "naive", "batch", "bwd_direct", "recur", "simt", "bwd_simt")
+GEMM_KERNELS = ("gemm", "bwd_gemm", "batch_sep")
+
+
+def alu_recipe(kernel):
+    """(updates per clk per SM at the nominal pipe rates, description, the
+    same bound as a function of the measured rates (m MUFU cosines, f FP32
+    multiply-adds per clk per SM), MUFU operations per update)."""
+    if kernel == "simt":
+        return (SIMT_PP_PER_CLK_PER_SM,
+                "FMA-pipe limit of the FP32 angle-addition product: 2 FP32 "
+                "multiply-adds per update, 128 per clk/SM", lambda m, f: f / 2.0, 0.0)
+    if kernel == "bwd_simt":
+        return (BWD_SIMT_PP_PER_CLK_PER_SM,
+                "FMA-pipe limit of the FP32 angle-addition adjoint: 4 FP32 "
+                "multiply-adds per update, 128 per clk/SM", lambda m, f: f / 4.0, 0.0)
+    if kernel == "recur":
+        return (RECUR_PP_PER_CLK_PER_SM,
+                "MUFU limit of the Eq. 2 recurrence recipe: 1 hardware cosine per "
+                "update at 16/clk/SM (7 issue slots per update allow 18.3)",
+                lambda m, f: m, 1.0)
+    if kernel == "bwd_direct":
+        return (ADJ_MIXED_PP_PER_CLK_PER_SM,
+                "FMA-pipe (128 FP32 ops/clk/SM) and MUFU (16 ops/clk/SM) limits of "
+                "the adjoint recipe: 5 FP32 ops + 2 MUFU (sin, cos) per hardware "
+                "update, 17 FP32 ops per polynomial update, best mix 11/28 -> 13.2 "
+                "updates/clk/SM", lambda m, f: (f + 6.0 * m) / 17.0, 2.0)
+    return (MIXED_PP_PER_CLK_PER_SM,
+            "FMA-pipe (128 FP32 ops/clk/SM) and MUFU (16 cosines/clk/SM) limits "
+            "of the direct recipe: 3 FP32 ops + 1 MUFU per MUFU-cosine update, "
+            "9 FP32 ops per polynomial-cosine update, best mix 5/14 -> 24.9 "
+            "updates/clk/SM", lambda m, f: (f + 6.0 * m) / 9.0, 1.0)
+
+
+def kernel_roofline(kernel, pp, flops, ms, sms, peaks, pipe_rates=None, sm_mhz=None):
+    """Roofline of one kernel from its algorithmic work per launch (pp
+    point-pixel updates, or flops for a tensor-core GEMM) and its mean launch
+    time in ms."""
+    if kernel in ALU_KERNELS and pp:
+        per_clk, src, measured, mufu_per_pp = alu_recipe(kernel)
+        achieved = pp / (ms / 1e3) / 1e9
+        peak = sms * per_clk * NOMINAL_MAX_MHZ * 1e6 / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Gpp/s", "frac": achieved / peak,
+                "peak_source": f"derived: {sms} SMs x {NOMINAL_MAX_MHZ:.0f} MHz max SM "
+                               f"clock x {per_clk:.2f} updates/clk/SM ({src})"}
+        if pipe_rates:
+            m, f = pipe_rates["mufu_cos_per_clk_per_sm"], pipe_rates["fma_per_clk_per_sm"]
+            roof["measured_pipe_rates"] = dict(pipe_rates)
+            roof["peak_from_measured_rates"] = (sms * measured(m, f) * NOMINAL_MAX_MHZ
+                                                * 1e6 / 1e9)
+            roof["frac_of_measured_rates"] = achieved / roof["peak_from_measured_rates"]
+        if mufu_per_pp:
+            roof["frac_mufu_only"] = achieved / (
+                sms * MUFU_PER_CLK_PER_SM / mufu_per_pp * NOMINAL_MAX_MHZ * 1e6 / 1e9)
+        if sm_mhz:
+            roof["frac_at_observed_clock"] = achieved / (sms * per_clk * sm_mhz * 1e6 / 1e9)
+        return roof
+    if kernel in GEMM_KERNELS and flops:
+        achieved = flops / (ms / 1e3) / 1e12
+        base = peaks.get("bf16_tflops")
+        src = "of measured (MEASURED_PEAKS.json bf16 burst; FP16 dense rate equal)"
+        if base is None:
+            base, src = 1900.0, "of fallback (1.9 PFLOP/s bf16)"
+        peak = base * FP16_OVER_BF16
+        return {"bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src}
+    return {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+            "unit": "GB/s", "frac": None}
+
+
+TUNABLE = ("direct", "sep_bf16", "sep_fp16", "sep_fp16x3")
+
+
+def prepare_legs(cg, h, which, methods, dev, stream, shard=None, tune=True):
+    """The legs of workload `which` that this build runs, each called once
+    (sizes workspaces, captures batch graphs); the device status checked.
+    tune: the library's autotuner picks the shapes first (direct tile, GEMM
+    plan, batch tiles), outside any timed region."""
+    import torch
+    c, all_legs = build_legs(cg, h, which, methods, dev, stream, shard)
+    legs = []
+    tuned = set()
+    for leg in all_legs:
+        try:
+            if tune and leg.size and leg.method in TUNABLE and \
+                    (leg.method, leg.size) not in tuned:
+                cg.cgh_tune(h, *leg.size, method=leg.method, stream=stream)
+                tuned.add((leg.method, leg.size))
+            if leg.problems and tune:
+                # the batch's tiles from the autotuner (outside any timed
+                # region; it synchronises)
+                m = leg.method.replace("batch_", "")
+                cg.cgh_tune_batch(h, leg.problems, m, stream=stream)
+                leg.plan = cg.cgh_batch_plan(h, leg.problems, m)
+            leg.fn()
+        except cg.CGHError as e:
+            if e.status == cg.CGH_ERR_UNSUPPORTED:
+                continue
+            raise
+        legs.append(leg)
+    if not legs:
+        raise SystemExit(f"no GPU method available for workload {which}")
+    torch.cuda.synchronize()
+    if cg.cgh_last_device_status(h) != cg.CGH_OK:
+        raise SystemExit("device status not OK after the first calls: "
+                         + cg.cgh_last_error(h))
+    return c, legs
+
+
+def time_legs(cg, h, legs, K, flush, stream):
+    """Per leg, two passes of K calls, each call after an L2 flush: the first
+    with events only around each call (ms per call, the call's kernels
+    overlapping as they do in use), the second with every kernel launch of
+    the handle bracketed by events as well (device time of each kernel).
+    Returns {leg name: (ms per call, {kernel: (total ms, launches)})}."""
+    import torch
+    out = {}
+    for leg in legs:
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            leg.fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+        cg.cgh_kernel_timing(h, True)
+        for _ in range(K):
+            flush.zero_()
+            leg.fn()
+        torch.cuda.synchronize()
+        kt = {name: cg.cgh_kernel_time(h, name) for name in cg.KERNELS}
+        cg.cgh_kernel_timing(h, False)
+        out[leg.name] = (ms, {k: v for k, v in kt.items() if v[1] > 0})
+    return out
+
+
+def leg_entries(legs, per_leg, K, sms, peaks, pipe_rates, sm_mhz):
+    """The "methods" object of a line: per leg its ms per call, point-pixel
+    updates per second, and its main kernel's device time per call and
+    roofline fraction (the call's work over that time; a kernel launched
+    more than once per call, like the adjoint's two GEMMs, is summed)."""
+    res = {}
+    for leg in legs:
+        ms, kt = per_leg[leg.name]
+        e = {"ms": ms, "pp_per_s": leg.pp / (ms / 1e3)}
+        k = leg.kernel
+        if k in kt:
+            kms = kt[k][0] / K
+            roof = kernel_roofline(k, leg.pp, leg.gemm_flops, kms, sms, peaks,
+                                   pipe_rates, sm_mhz)
+            e.update({"kernel": k, "kernel_ms_per_call": kms,
+                      "kernel_launches_per_call": kt[k][1] / K,
+                      "kernel_frac": roof["frac"], "kernel_bound": roof["bound"]})
+            if "frac_of_measured_rates" in roof:
+                e["kernel_frac_of_measured_rates"] = roof["frac_of_measured_rates"]
+        e["kernels_ms_per_launch"] = {n: v[0] / v[1] for n, v in kt.items()}
+        res[leg.name] = e
+    return res
+
+
+def dominant_kernel(legs, per_leg, K):
+    """The kernel with the most device time over the legs, its device time
+    per call of the legs it serves, and their work per call (mean pp; mean
+    GEMM flops)."""
+    tot = {}
+    for leg in legs:
+        for k, (ms, n) in per_leg[leg.name][1].items():
+            t = tot.setdefault(k, [0.0, 0])
+            t[0] += ms
+            t[1] += n
+    dom = max(tot, key=lambda k: tot[k][0])
+    served = [leg for leg in legs if leg.kernel == dom and dom in per_leg[leg.name][1]]
+    ncalls = K * max(1, len(served))
+    dom_ms = tot[dom][0] / ncalls
+    pp = statistics.mean(leg.pp for leg in served) if served else None
+    flops = statistics.mean(leg.gemm_flops for leg in served) if served else 0.0
+    launches = tot[dom][1] / ncalls
+    return dom, dom_ms, pp, flops, launches, {k: v[0] / v[1] for k, v in tot.items()}
+
+
+EXTRA_WORKLOADS = {
+    "large": ("3840x2160 pixels, N=16384 continuous points, z_j~U[0.3,2.0] m, "
+              "lambda=532 nm, p=3.74 um, seed 0", "direct,recur,sep_fp32,sep_bf16,"
+              "sep_fp16,sep_fp16x3"),
+    "batch64": ("64 holograms, Nx,Ny in {512..2048 step 128}, N~U[100,8192], lambda "
+                "in {633,532,473} nm, p=8 um, seed 0; one cgh_batch call each",
+                "direct,sep_fp16x3"),
+    "adjoint": ("1920x1080 pixels, N=4096 continuous points, lambda=532 nm, p=6.4 um, "
+                "seed 0; forward and adjoint (a seeded dL/dI field)",
+                "direct,sep_fp32,sep_fp16x3"),
+}
+
+
+def measure_extras(cg, h, dev, stream, flush, K, sms, peaks, pipe_rates, gpu_id,
+                   tune=True):
+    """The other workloads, measured leg by leg (ms per hologram or batch per
+    method, main kernel time and roofline fraction, the dominant kernel)."""
+    import torch
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.3)
+    t0 = time.time()
+    extra = {}
+    for which, (desc, methods) in EXTRA_WORKLOADS.items():
+        c, legs = prepare_legs(cg, h, which, methods.split(","), dev, stream, tune=tune)
+        for _ in range(2):
+            for leg in legs:
+                leg.fn()
+        torch.cuda.synchronize()
+        per_leg = time_legs(cg, h, legs, K, flush, stream)
+        dom, dom_ms, pp, flops, nl, _ = dominant_kernel(legs, per_leg, K)
+        roof = kernel_roofline(dom, pp, flops, dom_ms, sms, peaks, pipe_rates)
+        e = {"workload": desc, "pp_per_call": {leg.name: leg.pp for leg in legs},
+             "methods": leg_entries(legs, per_leg, K, sms, peaks, pipe_rates, None),
+             "dominant_kernel": {"kernel": dom, "ms_per_call": dom_ms,
+                                 "launches_per_call": nl,
+                                 "frac": roof["frac"], "bound": roof["bound"],
+                                 "peak": roof["peak"], "unit": roof["unit"]},
+             "steps": K, "l2": "flushed before every call"}
+        if which == "batch64":
+            e["batch_plans"] = {leg.name: leg.plan for leg in legs if leg.plan}
+        else:
+            e["shapes"] = {"direct_tile": list(cg.cgh_direct_tile_for(h, c.N, c.Nx, c.Ny)),
+                           "tuned": tune}
+            for m in sorted({leg.method for leg in legs if leg.method in GEMM_PASSES}):
+                e["shapes"]["gemm_plan_" + m] = list(cg.cgh_gemm_plan_for(h, c.N, c.Nx,
+                                                                          c.Ny, m))
+        if "frac_of_measured_rates" in roof:
+            e["dominant_kernel"]["frac_of_measured_rates"] = roof["frac_of_measured_rates"]
+        extra[which] = e
+        del legs
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    t1 = time.time()
+    extra["clocks"] = sampler.stop(t0, t1)
+    return extra
 
 
 def run_ours(args):
@@ -436,58 +723,43 @@ def run_ours(args):
                         "adjoint": "direct,sep_fp32,sep_fp16x3"}.get(args.workload,
                                                                      "direct,sep_fp16x3")
     methods = [m.strip() for m in args.methods.split(",") if m.strip()]
-    c, all_legs = build_legs(cg, h, args.workload, methods, dev, stream)
-    legs = []
-    for leg in all_legs:            # first call: sizes workspaces, builds graphs
-        try:
-            leg.fn()
-        except cg.CGHError as e:
-            if e.status == cg.CGH_ERR_UNSUPPORTED:
-                continue
-            raise
-        legs.append(leg)
-    if not legs:
-        raise SystemExit("no GPU method available")
-    torch.cuda.synchronize()
-    if cg.cgh_last_device_status(h) != cg.CGH_OK:
-        raise SystemExit("device status not OK after the first calls: "
-                         + cg.cgh_last_error(h))
+    shard = None
+    if world > 1 and args.split == "rows" and args.workload in ("paper", "large"):
+        from paper_1002_0916_gb300.sharding import row_slabs
+        from workloads import workload
+        Ny = workload(WORKLOAD if args.workload == "paper" else "cfg3_3840x2160_n16384").Ny
+        y0, rows = row_slabs(Ny, world)[rank]
+        shard = ("rows", y0, rows)
+    elif world > 1 and args.split == "problems" and args.workload == "batch64":
+        from paper_1002_0916_gb300.sharding import lpt_shard
+        from workloads import batch_problems
+        shard = ("problems", lpt_shard([cl.pp for cl in batch_problems(seed=0)], world)[rank])
+    c, legs = prepare_legs(cg, h, args.workload, methods, dev, stream, shard,
+                           tune=not args.no_tune)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB
 
-    def step(evs=None):
-        for i, leg in enumerate(legs):
+    def step():
+        for leg in legs:
             leg.fn()
-            if evs is not None:
-                evs[i + 1].record(stream)
 
     for _ in range(max(3, args.warmup)):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    # Which kernel dominates: a short pass with every launch bracketed by
-    # events (events between kernels stop launch overlap, so the timed
-    # steps below bracket only the dominant kernel).
-    cg.cgh_kernel_timing(h, True)
-    for _ in range(2):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    kt_all = {name: cg.cgh_kernel_time(h, name) for name in cg.KERNELS}
-    cg.cgh_kernel_timing(h, False)
-    dom = max((k for k in kt_all if kt_all[k][1] > 0), key=lambda k: kt_all[k][0])
 
-    # the two pipe rates the ALU rooflines are derived from, measured on this
-    # device (outside the timed region)
-    pipe_rates = None
-    if dom in ("direct", "naive", "batch", "bwd_direct", "recur", "simt", "bwd_simt"):
-        pipe_rates = cg.cgh_debug_pipe_rates(h, stream=stream)
     props = torch.cuda.get_device_properties(dev)
-    sampler = ClockSampler(f"GPU-{props.uuid}" if getattr(props, "uuid", None)
-                           else str(local))
+    sms = props.multi_processor_count
+    # the two pipe rates the ALU rooflines are derived from, measured on this
+    # device (outside the timed regions)
+    pipe_rates = cg.cgh_debug_pipe_rates(h, stream=stream)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    gpu_id = (f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local))
+    sampler = ClockSampler(gpu_id)
     K = args.steps
-    evsets = [[torch.cuda.Event(enable_timing=True) for _ in range(len(legs) + 1)]
-              for _ in range(K)]
     barrier()
     torch.cuda.synchronize()
     sampler.start()
@@ -498,28 +770,32 @@ def run_ours(args):
     while time.perf_counter() < t_end:
         step()
         torch.cuda.synchronize()
-    cg.cgh_kernel_timing_mask(h, [dom])
+
+    # ---- timed region 1: whole steps, events only at the step boundaries
+    # (nothing between the kernels of a step, so programmatic dependent
+    # launch overlaps each kernel's launch with the one before)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
     n0 = cg.cgh_launch_count(h)
     t0 = time.time()
-    for k in range(K):
+    for a, b in evs:
         flush.zero_()                       # L2 flush between timed steps
-        evsets[k][0].record(stream)
-        step(evsets[k])
+        a.record(stream)
+        step()
+        b.record(stream)
     torch.cuda.synchronize()
     t1 = time.time()
     launches = cg.cgh_launch_count(h) - n0
     barrier()
-    clocks = sampler.stop(t0, t1)
+    # ---- timed region 2: the same K steps leg by leg, each call and every
+    # kernel launch bracketed by events: ms per hologram per method and the
+    # dominant kernel's launch time for the roofline
+    per_leg = time_legs(cg, h, legs, K, flush, stream)
+    t2 = time.time()
+    barrier()
+    clocks = sampler.stop(t0, t2)
 
-    step_ms = [evs[0].elapsed_time(evs[-1]) for evs in evsets]
-    leg_ms = {leg.name: statistics.mean(evs[i].elapsed_time(evs[i + 1]) for evs in evsets)
-              for i, leg in enumerate(legs)}
-    kt = {name: cg.cgh_kernel_time(h, name) for name in cg.KERNELS}
-    cg.cgh_kernel_timing(h, False)
-    for k in kt:   # per-launch times of the other kernels: from the short pass
-        if k != dom:
-            kt[k] = kt_all[k]
-    ms = statistics.mean(step_ms)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
     if dist is not None:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -528,82 +804,23 @@ def run_ours(args):
         dist.all_reduce(lt, op=dist.ReduceOp.SUM)
         launches = int(lt.item())
     pp_step = sum(leg.pp for leg in legs)
-    value = world * pp_step / (ms / 1e3)
-
-    # ---- roofline of the dominant kernel (timed live in the timed steps)
-    dom_ms = kt[dom][0] / kt[dom][1]
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    sms = props.multi_processor_count
-    if dom in ("direct", "naive", "batch", "bwd_direct", "recur", "simt", "bwd_simt"):
-        # point-pixel updates per launch of the dominant kernel: the mean over
-        # the legs it serves (each leg launches it once per step)
-        dom_legs = [leg.pp for leg in legs if leg.kernel == dom]
-        pp_dom = statistics.mean(dom_legs) if dom_legs else c.pp
-        achieved = pp_dom / (dom_ms / 1e3) / 1e9
-        if dom == "simt":
-            per_clk = SIMT_PP_PER_CLK_PER_SM
-            src = ("FMA-pipe limit of the FP32 angle-addition product: 2 FP32 "
-                   "multiply-adds per update, 128 per clk/SM")
-        elif dom == "bwd_simt":
-            per_clk = BWD_SIMT_PP_PER_CLK_PER_SM
-            src = ("FMA-pipe limit of the FP32 angle-addition adjoint: 4 FP32 "
-                   "multiply-adds per update, 128 per clk/SM")
-        elif dom == "recur":
-            per_clk = RECUR_PP_PER_CLK_PER_SM
-            src = ("MUFU limit of the Eq. 2 recurrence recipe: 1 hardware cosine per "
-                   "update at 16/clk/SM (7 issue slots per update allow 18.3)")
-        elif dom == "bwd_direct":
-            per_clk = ADJ_MIXED_PP_PER_CLK_PER_SM
-            src = ("FMA-pipe (128 FP32 ops/clk/SM) and MUFU (16 ops/clk/SM) limits of "
-                   "the adjoint recipe: 5 FP32 ops + 2 MUFU (sin, cos) per hardware "
-                   "update, 17 FP32 ops per polynomial update, best mix 11/28 -> 13.2 "
-                   "updates/clk/SM")
-        else:
-            per_clk = MIXED_PP_PER_CLK_PER_SM
-            src = ("FMA-pipe (128 FP32 ops/clk/SM) and MUFU (16 cosines/clk/SM) limits "
-                   "of the direct recipe: 3 FP32 ops + 1 MUFU per MUFU-cosine update, "
-                   "9 FP32 ops per polynomial-cosine update, best mix 5/14 -> 24.9 "
-                   "updates/clk/SM")
-        peak = sms * per_clk * NOMINAL_MAX_MHZ * 1e6 / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Gpp/s", "frac": achieved / peak,
-                "peak_source": f"derived: {sms} SMs x {NOMINAL_MAX_MHZ:.0f} MHz max SM "
-                               f"clock x {per_clk:.2f} updates/clk/SM ({src})"}
-        if pipe_rates:
-            # the same recipe bound with the measured rates in place of the
-            # nominal 16 MUFU cosines and 128 FMAs per clock per SM
-            m, f = pipe_rates["mufu_cos_per_clk_per_sm"], pipe_rates["fma_per_clk_per_sm"]
-            per_clk_m = {"simt": f / 2.0, "bwd_simt": f / 4.0, "recur": m,
-                         "bwd_direct": (f + 6.0 * m) / 17.0}.get(dom, (f + 6.0 * m) / 9.0)
-            roof["measured_pipe_rates"] = dict(pipe_rates)
-            roof["peak_from_measured_rates"] = sms * per_clk_m * NOMINAL_MAX_MHZ * 1e6 / 1e9
-            roof["frac_of_measured_rates"] = achieved / roof["peak_from_measured_rates"]
-        if dom not in ("simt", "bwd_simt"):
-            mufu_per_pp = 2.0 if dom == "bwd_direct" else 1.0
-            roof["frac_mufu_only"] = achieved / (
-                sms * MUFU_PER_CLK_PER_SM / mufu_per_pp * NOMINAL_MAX_MHZ * 1e6 / 1e9)
-        if clocks and clocks.get("sm_mhz"):
-            roof["frac_at_observed_clock"] = achieved / (
-                sms * per_clk * clocks["sm_mhz"] * 1e6 / 1e9)
-    elif dom in ("gemm", "bwd_gemm"):
-        flops = sum(leg.gemm_flops for leg in legs)
-        nl = sum(leg.gemm_launches for leg in legs)
-        achieved = (flops / max(nl, 1)) / (dom_ms / 1e3) / 1e12
-        base = peaks.get("bf16_tflops")
-        src = "of measured (MEASURED_PEAKS.json bf16 burst; FP16 dense rate equal)"
-        if base is None:
-            base, src = 1900.0, "of fallback (1.9 PFLOP/s bf16)"
-        peak = base * FP16_OVER_BF16
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": src}
+    if shard is None:
+        value = world * pp_step / (ms / 1e3)     # replicas: every rank the whole step
     else:
-        roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": None}
+        # a split: the ranks' shares add up to one copy of the workload
+        from paper_1002_0916_gb300.sharding import reduce_sum
+        value = reduce_sum(pp_step, dist, dev) / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel (timed live in timed region 2)
+    dom, dom_ms, pp_dom, flops_dom, nl_dom, kernels_ms = dominant_kernel(legs, per_leg, K)
+    roof = kernel_roofline(dom, pp_dom, flops_dom, dom_ms, sms, peaks, pipe_rates,
+                           clocks.get("sm_mhz") if clocks else None)
     roof["kernel"] = dom
-    roof["ms_per_launch"] = dom_ms
+    roof["ms_per_launch"] = dom_ms / max(nl_dom, 1e-9)
+    roof["launches_per_call"] = nl_dom
+    roof["timed"] = ("timed region 2: K calls of each method with every kernel launch "
+                     "bracketed by CUDA events on its stream; achieved = the work of "
+                     "one call / the kernel's device time per call")
     roof["traffic"] = _traffic_for(dom)
 
     # ---- end to end through the host-buffer C-ABI call (forward legs)
@@ -693,6 +910,7 @@ def run_ours(args):
                                         + ", ".join(fwd_methods) + ")"}}
 
     table1 = None
+    leg_ms = {name: v[0] for name, v in per_leg.items()}
     if args.workload == "table1":
         from workloads import TABLE1_POINTS
         table1 = {"N": list(TABLE1_POINTS), "ms": {}, "pp_per_s": {},
@@ -709,16 +927,31 @@ def run_ours(args):
     if rank == 0:
         cfg = {"workload": workload_desc() if args.workload == "paper" else args.workload,
                "methods": [leg.name for leg in legs],
-               "l2": "flushed: 256 MiB device write between timed steps",
-               "parallelism": ("replicas (each rank its own copy of the workload)"
-                               if world > 1 else "single GPU")}
+               "l2": "flushed: 256 MiB device write between timed steps (and before "
+                     "every call of timed region 2)",
+               "parallelism": ("single GPU" if world == 1 else
+                               "replicas (each rank its own copy of the workload)"
+                               if shard is None else
+                               f"{world} ranks, each a slab of every hologram's rows "
+                               "(cgh_forward_rows), no collective on the data path"
+                               if shard[0] == "rows" else
+                               f"{world} ranks, each an LPT share of the batch's "
+                               "problems, no collective on the data path")}
+        if args.workload == "batch64":
+            cfg["batch_plans"] = {leg.name: leg.plan for leg in legs if leg.plan}
         if args.workload in ("paper", "large", "adjoint"):
-            cfg["direct_tile"] = dict(zip(
-                ("tile_x", "tile_y", "vec_x", "vec_y", "points_per_stage",
-                 "poly_pixels", "point_groups", "packed"),
-                cg.cgh_direct_tile_for(h, c.N, c.Nx, c.Ny)))
-            tiling, width = cg.cgh_gemm_plan(h, c.Nx, c.Ny)
-            cfg["gemm_tiles"] = {"tiling": tiling, "width": width}
+            Ny_call = shard[2] if shard is not None and shard[0] == "rows" else c.Ny
+            if Ny_call > 0:
+                cfg["direct_tile"] = dict(zip(
+                    ("tile_x", "tile_y", "vec_x", "vec_y", "points_per_stage",
+                     "poly_pixels", "point_groups", "packed"),
+                    cg.cgh_direct_tile_for(h, c.N, c.Nx, Ny_call)))
+                tiling, width, tuned_plan = cg.cgh_gemm_plan_for(h, c.N, c.Nx, Ny_call,
+                                                                 "sep_fp16x3")
+                cfg["gemm_plan_sep_fp16x3"] = {"tiling": tiling, "width": width,
+                                               "tuned": tuned_plan}
+            cfg["shapes"] = ("from the library's autotuner (cgh_tune)" if not args.no_tune
+                             else "the built-in heuristics")
         if args.workload == "table1":
             cfg["workload"] = ("1920x1024 pixels, N = 512, 1024, ..., 3584 points (the "
                                "paper's Table 1 sweep), otherwise the 1920x1024x1024 "
@@ -729,19 +962,26 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak",
+            "higher_is_better": True, "scaling": "weak" if shard is None else "strong",
             "vs_baseline": value / PAPER_PP_PER_S if args.workload == "paper" else None,
             "dtype": ("f32+f16x3" if any(leg.method in GEMM_PASSES for leg in legs)
                       else "f32"),
             "data": "synthetic", "config": cfg,
-            "methods": {leg.name: {"ms": leg_ms[leg.name],
-                                   "pp_per_s": leg.pp / (leg_ms[leg.name] / 1e3)}
-                        for leg in legs},
-            "kernels_ms_per_launch": {k: kt[k][0] / kt[k][1] for k in kt if kt[k][1] > 0},
+            "timing": ("ms_per_step, value, gpu_launches: timed region 1 (K whole steps, "
+                       "CUDA events only at step boundaries); methods, "
+                       "kernels_ms_per_launch, roofline: timed region 2 (the same K "
+                       "steps method by method, every call and kernel launch bracketed "
+                       "by events)"),
+            "methods": leg_entries(legs, per_leg, K, sms, peaks, pipe_rates, None),
+            "kernels_ms_per_launch": kernels_ms,
             "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         }
         if table1 is not None:
             line["table1"] = table1
+    if (rank == 0 and world == 1 and args.workload == "paper" and not args.no_extra):
+        line["extra"] = measure_extras(cg, h, dev, stream, flush, max(3, min(K, 5)),
+                                       sms, peaks, pipe_rates, gpu_id,
+                                       tune=not args.no_tune)
     cg.cgh_destroy(h)
     if dist is not None:
         dist.barrier()

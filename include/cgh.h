@@ -124,6 +124,19 @@ cgh_status cgh_forward(cgh_handle h, const float *points, const float *A,
                        const float *z, int N, double lambda, double p,
                        int Nx, int Ny, float *out, int method, void *stream);
 
+/* Rows y0 .. y0 + rows - 1 of the hologram of Eq. 1 (any height): the same
+ * values cgh_forward computes for those rows of a frame of at least
+ * y0 + rows rows, written to `out` (device, rows*Nx floats, row-major, row
+ * y0 first).  For a row split of one hologram over several GPUs, one
+ * process each: each computes its own slab with no exchange between them
+ * (pixel rows of Eq. 1 are independent).  The row origin is folded into the
+ * per-point records exactly (fixed-point turns, modulo one turn), so every
+ * method computes each pixel as cgh_forward does.  0 <= y0 <= 2^24;
+ * 1 <= rows <= 32768; other arguments and errors as cgh_forward. */
+cgh_status cgh_forward_rows(cgh_handle h, const float *points, const float *A,
+                            const float *z, int N, double lambda, double p, int Nx,
+                            int y0, int rows, float *out, int method, void *stream);
+
 /* cgh_forward from HOST buffers (Ny*Nx floats out), synchronising the
  * stream before returning.  Page-locked host buffers that are mapped into
  * the device's address space (cudaHostAlloc / cudaHostRegister memory,
@@ -330,7 +343,16 @@ cgh_status cgh_set_direct_schedule(cgh_handle h, int schedule);
  *                    issued for both SMs at once (tcgen05 cta_group::2), so
  *                    that each SM loads half as many operand bytes per
  *                    multiply-add;
- *   CGH_GEMM_AUTO:   CTA pairs for single holograms and adjoints of more
+ *   CGH_GEMM_PAIRS_GEN: CTA pairs whose producer warps compute each K
+ *                    block's U and V tiles (the separable form's operand
+ *                    tables, Eq. 1 split into its x and y phases) straight
+ *                    into shared memory from the point records, instead of
+ *                    a table kernel writing them to global memory and the
+ *                    GEMM reading them back; same entry values bit for bit,
+ *                    so the same hologram (single hologram forward only;
+ *                    the adjoint and cgh_batch take CGH_GEMM_PAIRS then);
+ *   CGH_GEMM_AUTO:   the handle's tuned plan for the size (cgh_tune), else
+ *                    CTA pairs for single holograms and adjoints of more
  *                    than 128 rows, one-CTA tiles otherwise and for
  *                    cgh_batch (whose persistent work list balances better
  *                    with the smaller items).
@@ -339,7 +361,8 @@ cgh_status cgh_set_direct_schedule(cgh_handle h, int schedule);
 typedef enum {
     CGH_GEMM_AUTO = 0,
     CGH_GEMM_SINGLE = 1,
-    CGH_GEMM_PAIRS = 2
+    CGH_GEMM_PAIRS = 2,
+    CGH_GEMM_PAIRS_GEN = 3
 } cgh_gemm_tiles;
 
 /* Select the GEMM tiling for later calls on this handle (also used by
@@ -347,12 +370,32 @@ typedef enum {
  * value. */
 cgh_status cgh_set_gemm_tiles(cgh_handle h, int tiles);
 
+/* Force a GEMM tiling and tile width for the separable forward methods of
+ * this handle (CGH_GEMM_AUTO: back to the tuned plan or the heuristic).
+ * Widths: 112 or 128 for CGH_GEMM_SINGLE; 112, 144, 160, 224 or 256 for
+ * CGH_GEMM_PAIRS and CGH_GEMM_PAIRS_GEN (the single-pass generating kernel
+ * has 112 and 256 only: other widths fall back to its heuristic there);
+ * width 0: the heuristic's width for the tiling.
+ * CGH_ERR_UNSUPPORTED for a plan not compiled in, CGH_ERR_INVALID_ARG for a
+ * null handle. */
+cgh_status cgh_set_gemm_plan(cgh_handle h, int tiling, int width);
+
 /* The tiling a separable forward GEMM of an Ny-row, Nx-column hologram
  * takes on this handle under its current setting: *tiling receives
  * CGH_GEMM_SINGLE or CGH_GEMM_PAIRS and *width the tile width (hologram
  * columns per tile).  CGH_ERR_INVALID_ARG for a null pointer or a size
  * below 1. */
 cgh_status cgh_gemm_plan(cgh_handle h, int Nx, int Ny, int *tiling, int *width);
+
+/* The GEMM plan a separable forward of `method` (CGH_SEP_BF16, CGH_SEP_FP16,
+ * CGH_SEP_FP16X3) with N points on an Nx x Ny frame takes on this handle:
+ * the forced tiling's, else the plan cgh_tune measured fastest for the size
+ * bucket, else the heuristic's.  *tiling receives CGH_GEMM_SINGLE,
+ * CGH_GEMM_PAIRS or CGH_GEMM_PAIRS_GEN, *width the tile width, *tuned (may
+ * be NULL) 1 if the plan came from the tuner.  CGH_ERR_INVALID_ARG for a
+ * null pointer, bad sizes or another method. */
+cgh_status cgh_gemm_plan_for(cgh_handle h, int method, int N, int Nx, int Ny,
+                             int *tiling, int *width, int *tuned);
 
 /* Number of direct-kernel tile shapes compiled into this library, and the
  * i-th of them (0 <= i < count). */
@@ -370,12 +413,21 @@ cgh_status cgh_direct_tile_for(cgh_handle h, int N, int Nx, int Ny,
  * Errors: CGH_ERR_UNSUPPORTED if the shape is not compiled in. */
 cgh_status cgh_set_direct_tile(cgh_handle h, const cgh_direct_tile *tile);
 
-/* Autotuner: time every compiled tile shape (CUDA events on `stream`,
- * synchronising it) for a problem of this size, remember the fastest for
- * the size bucket, and write it to *chosen (may be NULL).  The choice is
- * kept in the handle and, if the environment variable CGH_TUNE_CACHE names
- * a file, appended there as one JSON object per line (device name, size
- * bucket, tile) and read back by later handles. */
+/* Autotuner (the paper fixed its shapes -- 16 x 16 items per group, 256
+ * points per stage -- Section 2.1; here they are measured per size).
+ * method CGH_DIRECT_FP32: time every compiled direct tile shape (CUDA events
+ * on `stream`, synchronising it) for a problem of this size, remember the
+ * fastest for the size bucket, and write it to *chosen (may be NULL).
+ * method CGH_SEP_BF16 / CGH_SEP_FP16 / CGH_SEP_FP16X3: time the whole
+ * separable forward under every GEMM plan compiled in (one-CTA tiles 112
+ * and 128 wide, CTA pairs 112-256 wide, CTA pairs generating their operand
+ * tiles) and remember the fastest for the size bucket; later calls of that
+ * method and size on this handle use it while the GEMM tiling is
+ * CGH_GEMM_AUTO (read it back with cgh_gemm_plan_for); *chosen, if not NULL,
+ * is zeroed.  Choices are kept in the handle and, if the environment
+ * variable CGH_TUNE_CACHE names a file, appended there as one JSON object
+ * per line (device name, size bucket, tile or GEMM plan) and read back by
+ * later handles.  Other methods: CGH_ERR_UNSUPPORTED. */
 cgh_status cgh_tune(cgh_handle h, int N, int Nx, int Ny, int method,
                     void *stream, cgh_direct_tile *chosen);
 
@@ -416,12 +468,28 @@ cgh_status cgh_kernel_timing_mask(cgh_handle h, uint32_t mask);
 cgh_status cgh_kernel_time(cgh_handle h, int kernel, double *total_ms,
                            uint64_t *launches);
 
-/* Autotuner for cgh_batch with CGH_DIRECT_FP32: time every compiled tile
+/* Autotuner for cgh_batch.  CGH_DIRECT_FP32: time every compiled tile
  * shape on this batch (its geometry and data; synchronises `stream`), keep
  * the fastest for batches of the same sizes, write it to *chosen (may be
- * NULL).  Errors as cgh_batch; CGH_ERR_UNSUPPORTED for other methods. */
+ * NULL).  CGH_SEP_FP16X3: time the persistent grouped GEMM's two item
+ * shapes (one-CTA 128 x 128 items and CTA-pair 256 x 128 items) and keep
+ * the faster for batches of the same sizes (*chosen, if not NULL, is
+ * zeroed).  Later cgh_batch calls of that method and these sizes use the
+ * choice (with the GEMM tiling CGH_GEMM_AUTO for the separable batch);
+ * cgh_batch_plan reports it.  Errors as cgh_batch. */
 cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs, int count,
                           int method, void *stream, cgh_direct_tile *chosen);
+
+/* What cgh_batch would run for this batch: CGH_DIRECT_FP32 writes the
+ * direct tile shape to *tile (forced, tuned or the heuristic's) and 0 to
+ * *gemm_tiling; CGH_SEP_FP16X3 writes CGH_GEMM_SINGLE (one-CTA items) or
+ * CGH_GEMM_PAIRS (CTA-pair items) to *gemm_tiling and zeroes *tile.  *tuned
+ * = 1 when the choice came from cgh_tune_batch (or its cache file), else 0.
+ * Any output pointer may be NULL.  CGH_ERR_INVALID_ARG for a null handle or
+ * problem array, a count outside [1, 4096] or another method. */
+cgh_status cgh_batch_plan(cgh_handle h, const cgh_problem *probs, int count,
+                          int method, cgh_direct_tile *tile, int *gemm_tiling,
+                          int *tuned);
 
 /* Synchronise `stream`, then read and clear the handle's device status
  * word: CGH_OK, CGH_ERR_INVALID_ARG (a point had z <= 0 or a non-finite

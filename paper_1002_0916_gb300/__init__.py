@@ -33,6 +33,7 @@ __all__ = [
     "cgh_kernel_timing_mask", "cgh_set_gemm_tiles", "GEMM_TILES",
     "cgh_debug_pipe_rates", "cgh_direct_tile_for", "cgh_forward_host_async",
     "cgh_host_wait", "cgh_gemm_plan", "cgh_host_ticket", "cgh_host_wait_ticket",
+    "cgh_gemm_plan_for", "cgh_batch_plan", "cgh_set_gemm_plan", "cgh_forward_rows",
 ]
 
 CGH_OK, CGH_ERR_INVALID_ARG, CGH_ERR_CUDA = 0, 1, 2
@@ -82,6 +83,8 @@ def _load():
     L.cgh_forward.argtypes = [vp, fp, fp, fp, ci, cd, cd, ci, ci, fp, ci, vp]
     L.cgh_forward_host.argtypes = L.cgh_forward.argtypes
     L.cgh_forward_host_async.argtypes = L.cgh_forward.argtypes
+    L.cgh_forward_rows.argtypes = [vp, fp, fp, fp, ci, cd, cd, ci, ci, ci, fp, ci, vp]
+    L.cgh_forward_rows.restype = ci
     L.cgh_host_wait.argtypes = [vp, vp]
     L.cgh_host_ticket.argtypes = [vp]
     L.cgh_host_ticket.restype = ctypes.c_uint64
@@ -99,6 +102,15 @@ def _load():
     L.cgh_set_gemm_tiles.argtypes = [vp, ci]
     L.cgh_set_gemm_tiles.restype = ci
     L.cgh_gemm_plan.argtypes = [vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.cgh_gemm_plan_for.argtypes = [vp, ci, ci, ci, ci, ctypes.POINTER(ci),
+                                    ctypes.POINTER(ci), ctypes.POINTER(ci)]
+    L.cgh_gemm_plan_for.restype = ci
+    L.cgh_set_gemm_plan.argtypes = [vp, ci, ci]
+    L.cgh_set_gemm_plan.restype = ci
+    L.cgh_batch_plan.argtypes = [vp, ctypes.POINTER(_Problem), ci, ci,
+                                 ctypes.POINTER(_Tile), ctypes.POINTER(ci),
+                                 ctypes.POINTER(ci)]
+    L.cgh_batch_plan.restype = ci
     L.cgh_gemm_plan.restype = ci
     L.cgh_debug_pipe_rates.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), vp]
@@ -239,6 +251,23 @@ def cgh_forward(points, A, z, lam: float, p: float, Nx: int, Ny: int, *,
     return out
 
 
+def cgh_forward_rows(points, A, z, lam: float, p: float, Nx: int, y0: int, rows: int,
+                     *, out=None, method="direct", handle=None, stream=None):
+    """Rows y0 .. y0 + rows - 1 of the hologram of Eq. 1 (a slab of a row
+    split over GPUs); returns (or fills) out (rows, Nx) float32."""
+    torch = _torch()
+    N = int(A.numel())
+    if out is None:
+        out = torch.empty((rows, Nx), dtype=torch.float32, device=A.device)
+    h = handle if handle is not None else default_handle(A.device.index)
+    st = _L().cgh_forward_rows(h, _dev_f32(points, "points", 2 * N), _dev_f32(A, "A", N),
+                              _dev_f32(z, "z", N), N, float(lam), float(p), int(Nx),
+                              int(y0), int(rows), _dev_f32(out, "out", Nx * rows),
+                              _method(method), _stream_ptr(stream))
+    _check(h, st, "cgh_forward_rows")
+    return out
+
+
 def _host_ptr(a, name, n):
     import numpy as np
     if hasattr(a, "data_ptr"):
@@ -356,14 +385,34 @@ def cgh_batch(problems: Sequence[dict], *, method="direct", handle=None,
 
 
 def cgh_tune_batch(h, problems: Sequence[dict], method="direct", stream=None):
-    """Time every direct tile shape on this batch; returns the fastest."""
+    """Tune this batch: "direct" times every direct tile shape and returns
+    the fastest; "sep_fp16x3" times one-CTA and CTA-pair GEMM items and
+    returns the faster tiling ("single" or "pairs")."""
     arr, n = _problems(problems)
     t = _Tile()
     st = _L().cgh_tune_batch(h, arr, n, _method(method), _stream_ptr(stream),
                              ctypes.byref(t))
     _check(h, st, "cgh_tune_batch")
+    if _method(method) == METHODS["sep_fp16x3"]:
+        return cgh_batch_plan(h, problems, method)["gemm_tiling"]
     return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels,
             t.point_groups, t.packed)
+
+
+def cgh_batch_plan(h, problems: Sequence[dict], method="direct") -> dict:
+    """What cgh_batch runs for this batch: {"tile": direct tile shape or
+    None, "gemm_tiling": "single"/"pairs" or None, "tuned": bool}."""
+    arr, n = _problems(problems)
+    t, g, tu = _Tile(), ctypes.c_int(), ctypes.c_int()
+    st = _L().cgh_batch_plan(h, arr, n, _method(method), ctypes.byref(t),
+                             ctypes.byref(g), ctypes.byref(tu))
+    _check(h, st, "cgh_batch_plan")
+    direct = _method(method) == METHODS["direct"]
+    return {"tile": (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage,
+                     t.poly_pixels, t.point_groups, t.packed) if direct else None,
+            "gemm_tiling": None if direct else
+            {v: k for k, v in GEMM_TILES.items()}[g.value],
+            "tuned": bool(tu.value)}
 
 
 # ---------------------------------------------------------- tiles/tuning
@@ -417,13 +466,15 @@ def cgh_debug_pipe_rates(h, stream=None) -> dict:
     return {"mufu_cos_per_clk_per_sm": mufu.value, "fma_per_clk_per_sm": fma.value}
 
 
-GEMM_TILES = {"auto": 0, "single": 1, "pairs": 2}
+GEMM_TILES = {"auto": 0, "single": 1, "pairs": 2, "pairs_gen": 3}
 
 
 def cgh_set_gemm_tiles(h, tiles="auto"):
     """Tiling of the separable methods' tensor-core GEMM: "single" (one CTA
     per 128-row tile), "pairs" (two CTAs of a cluster per 256-row tile,
-    tcgen05 cta_group::2) or "auto"."""
+    tcgen05 cta_group::2), "pairs_gen" (pairs that generate their operand
+    tiles in shared memory, no U/V tables) or "auto" (tuned plan, else the
+    heuristic)."""
     st = _L().cgh_set_gemm_tiles(h, GEMM_TILES[tiles])
     _check(h, st, "cgh_set_gemm_tiles")
 
@@ -437,11 +488,34 @@ def cgh_gemm_plan(h, Nx: int, Ny: int):
     return {v: k for k, v in GEMM_TILES.items()}[t.value], w.value
 
 
+def cgh_set_gemm_plan(h, tiling="auto", width=0):
+    """Force the separable GEMM's tiling ("single", "pairs", "pairs_gen")
+    and tile width; "auto" returns to the tuned plan or the heuristic."""
+    st = _L().cgh_set_gemm_plan(h, GEMM_TILES[tiling], int(width))
+    _check(h, st, "cgh_set_gemm_plan")
+
+
+def cgh_gemm_plan_for(h, N: int, Nx: int, Ny: int, method="sep_fp16x3"):
+    """(tiling, width, tuned) of the separable forward GEMM of `method` for
+    N points on an Nx x Ny frame on this handle."""
+    t, w, tu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(h, _L().cgh_gemm_plan_for(h, _method(method), int(N), int(Nx), int(Ny),
+                                     ctypes.byref(t), ctypes.byref(w), ctypes.byref(tu)),
+           "cgh_gemm_plan_for")
+    return {v: k for k, v in GEMM_TILES.items()}[t.value], w.value, bool(tu.value)
+
+
 def cgh_tune(h, N: int, Nx: int, Ny: int, method="direct", stream=None):
+    """Measure the tunable shapes of `method` for this size and keep the
+    fastest on the handle: the direct tile (returned), or for the
+    tensor-core methods the GEMM plan (returned as cgh_gemm_plan_for's
+    (tiling, width, tuned))."""
     t = _Tile()
     st = _L().cgh_tune(h, int(N), int(Nx), int(Ny), _method(method),
                       _stream_ptr(stream), ctypes.byref(t))
     _check(h, st, "cgh_tune")
+    if _method(method) != METHODS["direct"]:
+        return cgh_gemm_plan_for(h, N, Nx, Ny, method)
     return (t.tile_x, t.tile_y, t.vec_x, t.vec_y, t.points_per_stage, t.poly_pixels,
             t.point_groups, t.packed)
 

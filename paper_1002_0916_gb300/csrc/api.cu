@@ -145,7 +145,7 @@ cgh_status cgh_ctx::forward_direct(const float *points, const float *A,
     if (!direct_fused_tables) {
         TimedLaunch tl(this, CGH_K_PROLOGUE, s);
         cudaError_t e = launch_prologue(points, A, z, N, Npad, lambda, p, rec,
-                                        d_status, s);
+                                        d_status, s, row_origin);
         if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
         tl.done();
     }
@@ -155,7 +155,7 @@ cgh_status cgh_ctx::forward_direct(const float *points, const float *A,
         cudaError_t e =
             direct_fused_tables
                 ? launch_direct_tables_fused(
-                      PointSource{points, A, z, N, lambda, p, d_status}, Npad, Nx, Ny,
+                      PointSource{points, A, z, N, lambda, p, d_status, row_origin}, Npad, Nx, Ny,
                       t, phx, phy, amp, count, nsplit, s)
                 : launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp, count,
                                        nsplit, s);
@@ -183,7 +183,7 @@ cgh_status cgh_ctx::forward_naive(const float *points, const float *A,
     {
         TimedLaunch tl(this, CGH_K_PROLOGUE, s);
         cudaError_t e = launch_prologue(points, A, z, N, N, lambda, p, rec,
-                                        d_status, s);
+                                        d_status, s, row_origin);
         if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
         tl.done();
     }
@@ -208,7 +208,7 @@ cgh_status cgh_ctx::forward_recur(const float *points, const float *A,
     {
         TimedLaunch tl(this, CGH_K_PROLOGUE, s);
         cudaError_t e = launch_prologue(points, A, z, N, Npad, lambda, p, rec,
-                                        d_status, s);
+                                        d_status, s, row_origin);
         if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
         tl.done();
     }
@@ -396,7 +396,7 @@ cgh_status cgh_create(cgh_handle *out, int device) {
     if (const char *f = getenv("CGH_SIMT_STAGE")) h->simt_stage = atoi(f);
     if (const char *f = getenv("CGH_GEMM_TILES")) {
         const int v = atoi(f);
-        if (v >= CGH_GEMM_AUTO && v <= CGH_GEMM_PAIRS) h->gemm_tiles = v;
+        if (v >= CGH_GEMM_AUTO && v <= CGH_GEMM_PAIRS_GEN) h->gemm_tiles = v;
     }
     if (const char *f = getenv("CGH_BWD_STAGED")) h->bwd_staged = atoi(f) != 0;
     if (const char *f = getenv("CGH_DIRECT_FUSED_TABLES"))
@@ -431,6 +431,23 @@ cgh_status cgh_forward(cgh_handle h, const float *points, const float *A,
     h->err[0] = 0;
     return h->forward(points, A, z, N, lambda, p, Nx, Ny, out, method,
                       (cudaStream_t)stream);
+}
+
+cgh_status cgh_forward_rows(cgh_handle h, const float *points, const float *A,
+                            const float *z, int N, double lambda, double p, int Nx,
+                            int y0, int rows, float *out, int method, void *stream) {
+    NvtxRange range("cgh_forward_rows");
+    if (!h) return CGH_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    h->err[0] = 0;
+    if (y0 < 0 || y0 > CGH_MAX_ROW_ORIGIN)
+        return h->fail(CGH_ERR_INVALID_ARG, "row origin %d outside [0, %d]", y0,
+                       CGH_MAX_ROW_ORIGIN);
+    h->row_origin = y0;
+    const cgh_status st = h->forward(points, A, z, N, lambda, p, Nx, rows, out, method,
+                                     (cudaStream_t)stream);
+    h->row_origin = 0;
+    return st;
 }
 
 // The device address of page-locked host memory mapped into the device's
@@ -738,11 +755,44 @@ cgh_status cgh_gemm_plan(cgh_handle h, int Nx, int Ny, int *tiling, int *width) 
     return CGH_OK;
 }
 
+cgh_status cgh_gemm_plan_for(cgh_handle h, int method, int N, int Nx, int Ny,
+                             int *tiling, int *width, int *tuned) {
+    if (!h || !tiling || !width || N < 1 || N > CGH_MAX_POINTS || Nx < 1 || Ny < 1 ||
+        Nx > CGH_MAX_SIDE || Ny > CGH_MAX_SIDE ||
+        (method != CGH_SEP_BF16 && method != CGH_SEP_FP16 && method != CGH_SEP_FP16X3))
+        return CGH_ERR_INVALID_ARG;
+    const cgh_ctx::GemmPlanChoice p = h->sep_plan(method, N, Nx, Ny);
+    *tiling = p.tiling;
+    *width = p.bn;
+    if (tuned) *tuned = p.tuned ? 1 : 0;
+    return CGH_OK;
+}
+
 cgh_status cgh_set_gemm_tiles(cgh_handle h, int tiles) {
     if (!h) return CGH_ERR_INVALID_ARG;
-    if (tiles < CGH_GEMM_AUTO || tiles > CGH_GEMM_PAIRS)
+    if (tiles < CGH_GEMM_AUTO || tiles > CGH_GEMM_PAIRS_GEN)
         return h->fail(CGH_ERR_INVALID_ARG, "unknown GEMM tiling %d", tiles);
     h->gemm_tiles = tiles;
+    h->gemm_bn = 0;
+    return CGH_OK;
+}
+
+cgh_status cgh_set_gemm_plan(cgh_handle h, int tiling, int width) {
+    if (!h) return CGH_ERR_INVALID_ARG;
+    if (tiling == CGH_GEMM_AUTO) {
+        h->gemm_tiles = CGH_GEMM_AUTO;
+        h->gemm_bn = 0;
+        return CGH_OK;
+    }
+    bool ok = false;
+    if (tiling == CGH_GEMM_SINGLE) ok = width == 0 || width == 112 || width == 128;
+    else if (tiling == CGH_GEMM_PAIRS) ok = width == 0 || pair_width_ok(width);
+    else if (tiling == CGH_GEMM_PAIRS_GEN) ok = width == 0 || gen_pair_width_ok(2, width);
+    if (!ok)
+        return h->fail(CGH_ERR_UNSUPPORTED, "GEMM plan %d / width %d not compiled in",
+                       tiling, width);
+    h->gemm_tiles = tiling;
+    h->gemm_bn = width;
     return CGH_OK;
 }
 

@@ -17,6 +17,7 @@
 
 #define CGH_MAX_POINTS (1 << 24)
 #define CGH_MAX_SIDE 32768
+#define CGH_MAX_ROW_ORIGIN (1 << 24)
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -79,8 +80,13 @@ struct cgh_ctx {
     void timer_reset();
 
     int forced_tile = -1;                         // direct tile override
+    // origin of the pixel rows of the forward call in progress (nonzero only
+    // inside cgh_forward_rows): every point record is built for rows
+    // row_origin + v
+    int row_origin = 0;
     int direct_schedule = CGH_SCHED_AUTO;         // cgh_set_direct_schedule
     int gemm_tiles = CGH_GEMM_AUTO;               // cgh_set_gemm_tiles
+    int gemm_bn = 0;                              // cgh_set_gemm_plan width (0: heuristic)
     // polynomial (FMA-pipe) sin/cos columns of the direct adjoint's 16-column
     // strips: 0, 4 (default) or 6; CGH_BWD_POLY at cgh_create
     int bwd_poly = 4;
@@ -98,6 +104,10 @@ struct cgh_ctx {
     // fail (-1: never); set from CGH_FAIL_ALLOC_AFTER at cgh_create
     int fail_alloc_after = -1;
     std::unordered_map<std::string, int> tuned;   // size bucket -> tile
+    // size bucket (separable methods) or batch bucket -> GEMM plan, encoded
+    // as tiling * 1000 + width (cgh_tune, cgh_tune_batch, the cache file)
+    std::unordered_map<std::string, int> tuned_gemm;
+    int forced_plan = -1;  // encoded GEMM plan while cgh_tune measures it
 
     cgh_status fail(cgh_status st, const char *fmt, ...);
     cgh_status cuda_fail(cudaError_t e, const char *where);
@@ -127,13 +137,24 @@ struct cgh_ctx {
                                  const float *z, int N, double lambda, double p,
                                  int Nx, int Ny, float *out, int method,
                                  cudaStream_t s);
+    // The GEMM plan of a separable forward (CGH_SEP_*) of this size: the
+    // plan being tuned, else the forced tiling's, else the tuned one for the
+    // size bucket, else the heuristic's.  *tuned (may be null): from the tuner.
+    struct GemmPlanChoice {
+        int tiling, bn;
+        bool tuned;
+    };
+    GemmPlanChoice sep_plan(int method, int N, int Nx, int Ny);
+    // split-FP16 batch plan: CTA-pair items (true) or one-CTA items
+    bool batch_sep_pairs(const cgh_problem *probs, int count, bool *tuned);
+    int default_batch_tile(const cgh_problem *probs, int count);
 
     cgh_status batch(const cgh_problem *probs, int count, int method,
-                     cudaStream_t s, int forced_tile_index);
+                     cudaStream_t s, int forced_tile_index, int forced_pairs = -1);
     cgh_status batch_direct(const cgh_problem *probs, int count, cudaStream_t s,
                             int tile_index);
     cgh_status batch_separable(const cgh_problem *probs, int count,
-                               cudaStream_t s);
+                               cudaStream_t s, int pairs_override = -1);
     cgh_status ensure_host_stage(size_t bytes);
     cgh_status run_batch_graph(uint64_t key, size_t meta_b, int nkernels,
                                const std::function<void(char *)> &fill_stage,

@@ -91,9 +91,20 @@ void cgh_ctx::load_tune_cache() {
         const char *d = strstr(line, "\"device\": \"");
         const char *b = strstr(line, "\"bucket\": \"");
         const char *t = strstr(line, "\"tile\": [");
-        if (!d || !b || !t) continue;
+        const char *gm = strstr(line, "\"gemm\": [");
+        if (!d || !b || (!t && !gm)) continue;
         if (sscanf(d + 11, "%255[^\"]", dev) != 1) continue;
         if (sscanf(b + 11, "%127[^\"]", bucket) != 1) continue;
+        if (gm) {
+            // {"device": "...", "bucket": "...", "gemm": [tiling, width]}
+            int tiling, width;
+            if (sscanf(gm + 9, "%d , %d", &tiling, &width) != 2) continue;
+            if (strcmp(dev, device_name) != 0) continue;
+            if (tiling >= CGH_GEMM_SINGLE && tiling <= CGH_GEMM_PAIRS_GEN && width > 0 &&
+                width < 1000)
+                tuned_gemm[bucket] = tiling * 1000 + width;
+            continue;
+        }
         if (sscanf(t + 9, "%d , %d , %d , %d , %d , %d , %d , %d", &tx, &ty, &vx,
                    &vy, &pt, &np, &g, &pk) != 8)
             continue;
@@ -104,13 +115,79 @@ void cgh_ctx::load_tune_cache() {
     fclose(f);
 }
 
+// The separable methods: time every GEMM plan compiled in -- one-CTA tiles,
+// CTA pairs, CTA pairs generating their operand tiles -- at each width, on
+// the whole forward (prologue, tables if any, GEMM), and keep the fastest
+// for the size bucket.
+static cgh_status tune_separable(cgh_ctx *h, int N, int Nx, int Ny, int method,
+                                 cudaStream_t s, const float *pts, const float *A,
+                                 const float *z, float *out) {
+    const int kind = method == CGH_SEP_BF16 ? 0 : method == CGH_SEP_FP16 ? 1 : 2;
+    static const int widths[] = {112, 128, 144, 160, 224, 256};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    int best = -1;
+    cgh_status st = CGH_OK;
+    for (int tiling = CGH_GEMM_SINGLE; tiling <= CGH_GEMM_PAIRS_GEN && st == CGH_OK;
+         ++tiling) {
+        for (int w : widths) {
+            const bool ok = tiling == CGH_GEMM_SINGLE ? (w == 112 || w == 128)
+                            : tiling == CGH_GEMM_PAIRS ? pair_width_ok(w)
+                                                       : gen_pair_width_ok(kind, w);
+            if (!ok) continue;
+            h->forced_plan = tiling * 1000 + w;
+            st = h->forward_separable(pts, A, z, N, 532e-9, 8e-6, Nx, Ny, out, method, s);
+            float ms_i = 1e30f;
+            for (int r = 0; r < 3 && st == CGH_OK; ++r) {
+                cudaEventRecord(e0, s);
+                st = h->forward_separable(pts, A, z, N, 532e-9, 8e-6, Nx, Ny, out,
+                                          method, s);
+                cudaEventRecord(e1, s);
+                if (st) break;
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_i = ms < ms_i ? ms : ms_i;
+            }
+            if (st) break;
+            if (ms_i < best_ms) {
+                best_ms = ms_i;
+                best = h->forced_plan;
+            }
+        }
+    }
+    h->forced_plan = -1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaError_t e = cudaGetLastError();
+    if (st == CGH_OK && e != cudaSuccess) st = h->cuda_fail(e, "tuning");
+    if (st == CGH_OK && best >= 0) {
+        const std::string b = size_bucket(method, N, Nx, Ny);
+        h->tuned_gemm[b] = best;
+        if (const char *path = cache_path()) {
+            if (FILE *f = fopen(path, "a")) {
+                fprintf(f,
+                        "{\"device\": \"%s\", \"bucket\": \"%s\", \"gemm\": [%d, %d], "
+                        "\"ms\": %.5f}\n",
+                        h->device_name, b.c_str(), best / 1000, best % 1000, best_ms);
+                fclose(f);
+            }
+        }
+    }
+    return st;
+}
+
 extern "C" cgh_status cgh_tune(cgh_handle h, int N, int Nx, int Ny, int method,
                                void *stream, cgh_direct_tile *chosen) {
     NvtxRange range("cgh_tune");
     if (!h) return CGH_ERR_INVALID_ARG;
-    if (method != CGH_DIRECT_FP32)
+    const bool sep = method == CGH_SEP_BF16 || method == CGH_SEP_FP16 ||
+                     method == CGH_SEP_FP16X3;
+    if (method != CGH_DIRECT_FP32 && !sep)
         return h->fail(CGH_ERR_UNSUPPORTED,
-                       "only the direct method has tunable tiles");
+                       "only the direct and the tensor-core methods have tunable tiles");
     if (N < 1 || N > CGH_MAX_POINTS || Nx < 1 || Ny < 1 || Nx > CGH_MAX_SIDE ||
         Ny > CGH_MAX_SIDE)
         return h->fail(CGH_ERR_INVALID_ARG, "bad tuning size");
@@ -132,6 +209,12 @@ extern "C" cgh_status cgh_tune(cgh_handle h, int N, int Nx, int Ny, int method,
         TimedLaunch tl(h, CGH_K_AUX, s);
         tune_fill_kernel<<<(N + 127) / 128, 128, 0, s>>>(pts, A, z, N, Nx, Ny);
         tl.done();
+    }
+    if (sep) {
+        st = tune_separable(h, N, Nx, Ny, method, s, pts, A, z, out);
+        if (chosen) memset(chosen, 0, sizeof(*chosen));
+        cudaSetDevice(prev_dev);
+        return st;
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

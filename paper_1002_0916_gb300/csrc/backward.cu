@@ -775,7 +775,10 @@ static cgh_status run_backward(cgh_ctx *h, const float *points, const float *A,
         GemmOperands o2 = o1;
         o2.A_hi = Uhi; o2.A_lo = Ulo; o2.B_hi = Grh; o2.B_lo = Grl;
         o2.M = Kp; o2.N = Ny; o2.K = Nx; o2.lda = ldx; o2.ldb = ldx; o2.ldd = Ny;
-        o1.tiles = o2.tiles = h->gemm_tiles;
+        // (the generating GEMM is a forward kernel: the adjoint's GEMMs
+        // take CTA pairs then)
+        o1.tiles = o2.tiles =
+            h->gemm_tiles == CGH_GEMM_PAIRS_GEN ? CGH_GEMM_PAIRS : h->gemm_tiles;
         int wx = 128, wy = 128;  // column width of one partial-sum tile
         {
             TimedLaunch tl(h, CGH_K_BWD_GEMM, s);

@@ -381,7 +381,7 @@ cgh_status cgh_ctx::batch_direct(const cgh_problem *probs, int count,
 }
 
 cgh_status cgh_ctx::batch(const cgh_problem *probs, int count, int method,
-                          cudaStream_t s, int forced_tile_index) {
+                          cudaStream_t s, int forced_tile_index, int forced_pairs) {
     if (count < 1 || count > 4096 || !probs)
         return fail(CGH_ERR_INVALID_ARG, "batch count %d outside [1, 4096]", count);
     for (int i = 0; i < count; ++i) {
@@ -402,22 +402,25 @@ cgh_status cgh_ctx::batch(const cgh_problem *probs, int count, int method,
             if (it != tuned.end()) {
                 ti = it->second;
             } else {
-                // untuned: the heuristic's shape for the problem with the most
-                // work (persistent CTAs balance the rest)
-                int big = 0;
-                for (int i = 1; i < count; ++i)
-                    if ((double)probs[i].N * probs[i].Nx * probs[i].Ny >
-                        (double)probs[big].N * probs[big].Nx * probs[big].Ny)
-                        big = i;
-                ti = default_direct_tile(probs[big].N, probs[big].Nx, probs[big].Ny,
-                                         sm_count);
+                ti = default_batch_tile(probs, count);
             }
         }
         return batch_direct(probs, count, s, ti);
     }
-    if (method == CGH_SEP_FP16X3) return batch_separable(probs, count, s);
+    if (method == CGH_SEP_FP16X3) return batch_separable(probs, count, s, forced_pairs);
     return fail(CGH_ERR_INVALID_ARG,
                 "batch method must be CGH_DIRECT_FP32 or CGH_SEP_FP16X3");
+}
+
+// Untuned: the heuristic's shape for the problem with the most work
+// (persistent CTAs balance the rest).
+int cgh_ctx::default_batch_tile(const cgh_problem *probs, int count) {
+    int big = 0;
+    for (int i = 1; i < count; ++i)
+        if ((double)probs[i].N * probs[i].Nx * probs[i].Ny >
+            (double)probs[big].N * probs[big].Nx * probs[big].Ny)
+            big = i;
+    return default_direct_tile(probs[big].N, probs[big].Nx, probs[big].Ny, sm_count);
 }
 
 std::string batch_bucket(const cgh_problem *probs, int count) {
@@ -444,17 +447,85 @@ extern "C" cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int coun
     return st;
 }
 
+extern "C" cgh_status cgh_batch_plan(cgh_handle h, const cgh_problem *probs, int count,
+                                     int method, cgh_direct_tile *tile, int *gemm_tiling,
+                                     int *tuned) {
+    if (!h || !probs || count < 1 || count > 4096) return CGH_ERR_INVALID_ARG;
+    if (tuned) *tuned = 0;
+    if (method == CGH_DIRECT_FP32) {
+        int ti = h->forced_tile;
+        if (ti < 0) {
+            auto it = h->tuned.find(batch_bucket(probs, count));
+            if (it != h->tuned.end()) {
+                ti = it->second;
+                if (tuned) *tuned = 1;
+            } else {
+                ti = h->default_batch_tile(probs, count);
+            }
+        }
+        if (gemm_tiling) *gemm_tiling = 0;
+        return tile ? cgh_direct_tile_get(ti, tile) : CGH_OK;
+    }
+    if (method == CGH_SEP_FP16X3) {
+        bool tu = false;
+        const bool pairs = h->batch_sep_pairs(probs, count, &tu);
+        if (gemm_tiling) *gemm_tiling = pairs ? CGH_GEMM_PAIRS : CGH_GEMM_SINGLE;
+        if (tuned) *tuned = tu ? 1 : 0;
+        if (tile) memset(tile, 0, sizeof(*tile));
+        return CGH_OK;
+    }
+    return CGH_ERR_INVALID_ARG;
+}
+
 extern "C" cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs,
                                      int count, int method, void *stream,
                                      cgh_direct_tile *chosen) {
     NvtxRange range("cgh_tune_batch");
     if (!h) return CGH_ERR_INVALID_ARG;
-    if (method != CGH_DIRECT_FP32)
-        return h->fail(CGH_ERR_UNSUPPORTED, "only the direct batch has tunable tiles");
+    if (method != CGH_DIRECT_FP32 && method != CGH_SEP_FP16X3)
+        return h->fail(CGH_ERR_INVALID_ARG,
+                       "batch method must be CGH_DIRECT_FP32 or CGH_SEP_FP16X3");
     int prev = 0;
     cudaGetDevice(&prev);
     if (prev != h->device) cudaSetDevice(h->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if (method == CGH_SEP_FP16X3) {
+        // the grouped split-FP16 GEMM's two item shapes: one-CTA items and
+        // CTA-pair items (each timed on its captured graph, best of three)
+        cgh_status st = CGH_OK;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        int best_pairs = -1;
+        for (int pairs = 0; pairs < 2 && st == CGH_OK; ++pairs) {
+            st = h->batch(probs, count, method, s, -1, pairs);  // builds the graph
+            float ms_p = 1e30f;
+            for (int r = 0; r < 3 && st == CGH_OK; ++r) {
+                cudaEventRecord(e0, s);
+                st = h->batch(probs, count, method, s, -1, pairs);
+                cudaEventRecord(e1, s);
+                if (st) break;
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_p = ms < ms_p ? ms : ms_p;
+            }
+            if (st == CGH_OK && ms_p < best) {
+                best = ms_p;
+                best_pairs = pairs;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st == CGH_OK && best_pairs >= 0)
+            h->tuned_gemm[batch_bucket(probs, count) + "_sep"] =
+                (best_pairs ? CGH_GEMM_PAIRS : CGH_GEMM_SINGLE) * 1000 +
+                (best_pairs ? group_pair_tile_n() : group_tile_n());
+        if (chosen) memset(chosen, 0, sizeof(*chosen));
+        if (prev != h->device) cudaSetDevice(prev);
+        return st;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -535,8 +606,24 @@ __global__ void sep_batch_tables_kernel(const SepPrep *__restrict__ prep) {
 
 // Split-FP16 batch: one prologue launch, one table launch, one persistent
 // grouped tensor-core GEMM (umma.cu) over (problem, m tile, n tile) items.
+bool cgh_ctx::batch_sep_pairs(const cgh_problem *probs, int count, bool *tuned_out) {
+    if (tuned_out) *tuned_out = false;
+    if (gemm_tiles == CGH_GEMM_PAIRS || gemm_tiles == CGH_GEMM_PAIRS_GEN) return true;
+    if (gemm_tiles == CGH_GEMM_SINGLE) return false;
+    auto it = tuned_gemm.find(batch_bucket(probs, count) + "_sep");
+    if (it != tuned_gemm.end()) {
+        if (tuned_out) *tuned_out = true;
+        return it->second / 1000 == CGH_GEMM_PAIRS;
+    }
+    // one-CTA items (128 x 128) unless CTA pairs were asked for: pair items
+    // (256 x 128) halve the number of work items, and on the 64-hologram
+    // batch the coarser balance cost more (4.55 ms) than the halved operand
+    // bytes per SM saved (one-CTA items: 4.24 ms)
+    return false;
+}
+
 cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, int pairs_override) {
     std::vector<SepPrep> prep;
     std::vector<size_t> offs;
     size_t ws_bytes = 0;
@@ -563,11 +650,8 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
     }
     cgh_status st = ensure(bws, ws_bytes > 0 ? ws_bytes : 256, s, "batch workspace");
     if (st) return st;
-    // one-CTA items (128 x 128) unless CTA pairs were asked for: pair items
-    // (256 x 128) halve the number of work items, and on the 64-hologram
-    // batch the coarser balance cost more (4.55 ms) than the halved operand
-    // bytes per SM saved (one-CTA items: 4.24 ms)
-    const bool pairs = gemm_tiles == CGH_GEMM_PAIRS;
+    const bool pairs = pairs_override >= 0 ? pairs_override != 0
+                                           : batch_sep_pairs(probs, count, nullptr);
     const int TM = pairs ? group_pair_tile_m() : 128;
     const int BN = pairs ? group_pair_tile_n() : group_tile_n();
     const int b_box = pairs ? group_pair_box_b() : group_tile_n();
@@ -604,7 +688,7 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
         op.lo_scale = 1.0f / LO_SCALE;
         op.D = probs[pidx[k]].out;
         op.ldd = sp.Nx;
-        op.tiles = gemm_tiles;
+        op.tiles = gemm_tiles == CGH_GEMM_PAIRS_GEN ? CGH_GEMM_PAIRS : gemm_tiles;
         ops[k] = op;
         if (!encode_group_prob(&gps[k], op, b_box))
             return fail(CGH_ERR_CUDA, "problem %d: tensor map encoding failed", pidx[k]);

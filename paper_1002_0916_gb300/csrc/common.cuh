@@ -171,11 +171,11 @@ struct DirectTile {
 // Number of points after padding to a multiple of `pt`.
 inline int pad_to(int n, int m) { return (n + m - 1) / m * m; }
 
-// prologue.cu
+// prologue.cu; y0: origin of the pixel rows (see make_point_rec)
 cudaError_t launch_prologue(const float *points, const float *A,
                             const float *z, int N, int Npad, double lambda,
                             double p, PointRec *rec, unsigned *status,
-                            cudaStream_t s);
+                            cudaStream_t s, int y0 = 0);
 
 // direct.cu
 int direct_tile_count();
@@ -194,6 +194,7 @@ struct PointSource {
     int N;
     double lambda, p;
     unsigned *status;
+    int y0 = 0;  // origin of the pixel rows (see make_point_rec)
 };
 // The same tables with the records built inside the kernel (no prologue).
 cudaError_t launch_direct_tables_fused(const PointSource &src, int Npad, int Nx,
@@ -237,6 +238,7 @@ struct GemmOperands {
     long long ldd;
     int tiles = CGH_GEMM_AUTO;  // a cgh_gemm_tiles value
     int accumulate = 0;         // 1: D += product instead of D = product
+    int bn = 0;                 // tile width of a tuned plan (0: the heuristic's)
 };
 bool gemm_operands_ok(const GemmOperands &op);
 // Longest K one launch accumulates in tensor memory.  The tensor cores' FP32
@@ -258,12 +260,26 @@ inline int gemm_k_chunks(int K, bool split) {
 // bnp = columns of a pair tile (one of the compiled widths)
 // The pair tile width for an M x N product and its cost (SM waves x width).
 int pick_pair_n(int M, int N, int sms, double *cost = nullptr);
+bool pair_width_ok(int bnp);
 // How launch_umma_gemm tiles an M x N forward product under a cgh_gemm_tiles
 // setting: CGH_GEMM_SINGLE or CGH_GEMM_PAIRS, and the tile width.
 struct GemmPlan {
     int tiling, bn;
 };
-GemmPlan gemm_plan(int M, int N, int tiles, int sms);
+// kind: 0 BF16, 1 FP16, 2 split FP16 (the widths compiled for the
+// generating kernel depend on it); bn: a width to use instead of the
+// heuristic's (0: none)
+GemmPlan gemm_plan(int M, int N, int tiles, int sms, int kind = 2, int bn = 0);
+// Cost of a pair width: SM waves x columns per CTA (umma2.cu).
+double pair_cost(int M, int N, int bnp, int sms);
+// umma_gen.cu: the pair GEMM with its operand tiles generated in shared
+// memory from the point records (no U / V tables): D = R L^T over the Npad
+// records at rec (N real), K chunks as launch_umma_gemm.
+bool gen_pair_width_ok(int kind, int bnp);
+int pick_gen_n(int M, int N, int sms, int kind);
+cudaError_t launch_umma_gen(const PointRec *rec, int N, int Npad, int kind, int bnp,
+                            float *D, int M, int Ncols, long long ldd, float lo_scale,
+                            unsigned *status, cudaStream_t s);
 cudaError_t launch_umma_pair(const GemmOperands &op, int bnp, unsigned *status,
                              cudaStream_t s);
 struct AdjEpiArgs;
@@ -282,9 +298,10 @@ cudaError_t launch_umma_adjoint(const GemmOperands &op, const PointRec *rec,
                                 cudaStream_t s, int *tile_n);
 int umma_tile_n();
 
-// separable.cu: U / V tables of the separable form.
-cudaError_t launch_sep_tables(const PointRec *rec, int N, int Npad, int Nx,
-                              int Ny, int Kp, int kind, void *Lhi, void *Llo,
-                              void *Rhi, void *Rlo, cudaStream_t s);
+// separable.cu: U / V tables of the separable form, the point records
+// built inside the kernel from the caller's points.
+cudaError_t launch_sep_tables(const PointSource &src, int Npad, int Nx, int Ny, int Kp,
+                              int kind, void *Lhi, void *Llo, void *Rhi, void *Rlo,
+                              cudaStream_t s);
 
 }  // namespace cgh

@@ -50,11 +50,16 @@ __device__ __forceinline__ uint64_t mul_shift(uint64_t c, uint64_t v, int s) {
 // Only Q_j itself is computed in FP64.  With c = Q_j in 0.64 fixed point
 // and u_j = m 2^-s exactly, the axis coefficients are exact integer
 // arithmetic on c: b = 2 c u_j and a = c u_j^2 (mod 1 turn).
+//
+// y0 != 0 moves the y origin: the record then gives the phase of pixel row
+// y0 + v at row index v, i.e. c (v + y0)^2 - b (v + y0) + a
+//   = c v^2 - (b - 2 c y0) v + (a - b y0 + c y0^2),
+// again exact modulo one turn (a slab of rows of a larger hologram).
 __device__ __forceinline__ PointRec make_point_rec(const float *points,
                                                    const float *A,
                                                    const float *z, int N, int j,
                                                    double lambda, double p,
-                                                   unsigned *status) {
+                                                   unsigned *status, int y0 = 0) {
     PointRec r;
     r.c = r.bx = r.ax = r.by = r.ay = 0;
     r.A = 0.0f;
@@ -77,6 +82,11 @@ __device__ __forceinline__ PointRec make_point_rec(const float *points,
             b = mul_shift(r.c, m, s) << 1;
             r.by = yj < 0.0f ? (uint64_t)0 - b : b;
             r.ay = mul_shift(r.c, m * m, 2 * s);
+            if (y0 != 0) {
+                const uint64_t Y = (uint64_t)(int64_t)y0;
+                r.ay = r.ay - r.by * Y + r.c * (Y * Y);
+                r.by = r.by - 2 * r.c * Y;
+            }
             r.A = aj;
             r.Q32 = (float)Q;
         } else {

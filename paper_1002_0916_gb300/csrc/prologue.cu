@@ -20,25 +20,25 @@ __global__ void prologue_kernel(const float *__restrict__ points,
                                 const float *__restrict__ z, int N, int Npad,
                                 double lambda, double p,
                                 PointRec *__restrict__ rec,
-                                unsigned *status) {
+                                unsigned *status, int y0) {
     pdl_wait();  // the inputs may come from the kernel before
     pdl_trigger();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Npad) return;
-    rec[j] = make_point_rec(points, A, z, N, j, lambda, p, status);
+    rec[j] = make_point_rec(points, A, z, N, j, lambda, p, status, y0);
 }
 
 cudaError_t launch_prologue(const float *points, const float *A,
                             const float *z, int N, int Npad, double lambda,
                             double p, PointRec *rec, unsigned *status,
-                            cudaStream_t s) {
+                            cudaStream_t s, int y0) {
     if (Npad <= 0) return cudaSuccess;
     // FP64 runs at a few operations per clock per SM on this GPU, so spread
     // the points thinly over many SMs
     int threads = 32;
     int blocks = (Npad + threads - 1) / threads;
     return launch_dependent(prologue_kernel, dim3(blocks), dim3(threads), 0, s, points,
-                            A, z, N, Npad, lambda, p, rec, status);
+                            A, z, N, Npad, lambda, p, rec, status, y0);
 }
 
 }  // namespace cgh

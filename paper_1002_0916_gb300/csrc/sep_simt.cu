@@ -434,7 +434,7 @@ cgh_status cgh_ctx::forward_simt(const float *points, const float *A,
     {
         TimedLaunch tl(this, CGH_K_PROLOGUE, s);
         cudaError_t e = launch_prologue(points, A, z, N, Npad, lambda, p, rec,
-                                        d_status, s);
+                                        d_status, s, row_origin);
         if (e != cudaSuccess) return cuda_fail(e, "prologue launch");
         tl.done();
     }

@@ -337,14 +337,18 @@ static int pick_tile_n(int M, int N, int sms) {
     return cost(112) < cost(128) ? 112 : 128;
 }
 
-GemmPlan gemm_plan(int M, int N, int tiles, int sms) {
+GemmPlan gemm_plan(int M, int N, int tiles, int sms, int kind, int bn) {
     // CTA pairs halve each SM's operand bytes per multiply-add; measured on
     // the 3840 x 2160 x 16384 product 1.9x (single pass) and 1.3x (split)
     // faster than one-CTA tiles, equal at 1920 x 1024 x 1024.  A frame of
     // at most 128 rows would leave half of every pair tile empty.
+    if (tiles == CGH_GEMM_PAIRS_GEN)
+        return GemmPlan{CGH_GEMM_PAIRS_GEN,
+                        gen_pair_width_ok(kind, bn) ? bn : pick_gen_n(M, N, sms, kind)};
     const bool pairs = tiles == CGH_GEMM_PAIRS || (tiles == CGH_GEMM_AUTO && M > 128);
-    if (!pairs) return GemmPlan{CGH_GEMM_SINGLE, pick_tile_n(M, N, sms)};
-    return GemmPlan{CGH_GEMM_PAIRS, pick_pair_n(M, N, sms)};
+    if (!pairs)
+        return GemmPlan{CGH_GEMM_SINGLE, (bn == 112 || bn == 128) ? bn : pick_tile_n(M, N, sms)};
+    return GemmPlan{CGH_GEMM_PAIRS, pair_width_ok(bn) ? bn : pick_pair_n(M, N, sms)};
 }
 
 cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
@@ -370,7 +374,8 @@ cudaError_t launch_umma_gemm(const GemmOperands &op, unsigned *status,
         return cudaSuccess;
     }
     AdjEpiArgs ea{};
-    const GemmPlan plan = gemm_plan(op.M, op.N, op.tiles, sm_count_of_current_device());
+    const GemmPlan plan = gemm_plan(op.M, op.N, op.tiles, sm_count_of_current_device(),
+                                    op.bf16 ? 0 : op.split ? 2 : 1, op.bn);
     if (plan.tiling == CGH_GEMM_PAIRS) return launch_umma_pair(op, plan.bn, status, s);
     const int bn = plan.bn;
     if (op.split)

@@ -159,6 +159,38 @@ def test_batch64_uneven_workload(cg, h, oracle_mod, method):
             assert rel <= 1e-4, i
 
 
+def test_tuned_separable_batch(cg, oracle_mod):
+    """cgh_tune_batch on the split-FP16 batch times both GEMM item shapes
+    and later calls of these sizes use the faster (cgh_batch_plan says so);
+    every hologram within the split-FP16 bound of the FP64 oracle (Eq. 1)."""
+    import torch
+    hh = cg.cgh_create(0)
+    try:
+        clouds = _small_clouds()
+        probs = _problems(clouds)
+        assert cg.cgh_batch_plan(hh, probs, "sep_fp16x3")["tuned"] is False
+        tiling = cg.cgh_tune_batch(hh, probs, "sep_fp16x3")
+        assert tiling in ("single", "pairs")
+        plan = cg.cgh_batch_plan(hh, probs, "sep_fp16x3")
+        assert plan["tuned"] is True and plan["gemm_tiling"] == tiling
+        for pr in probs:
+            pr["out"].fill_(float("nan"))
+        cg.cgh_batch(probs, method="sep_fp16x3", handle=hh)
+        torch.cuda.synchronize()
+        assert cg.cgh_last_device_status(hh) == cg.CGH_OK
+        for c, pr in zip(clouds, probs):
+            got = pr["out"].cpu().numpy()
+            if c.N == 0:
+                assert np.count_nonzero(got) == 0
+            else:
+                assert rel_rms(got, oracle_mod.forward(c)) <= 1e-4
+        tile = cg.cgh_tune_batch(hh, probs, "direct")
+        plan = cg.cgh_batch_plan(hh, probs, "direct")
+        assert plan["tuned"] is True and plan["tile"] == tile
+    finally:
+        cg.cgh_destroy(hh)
+
+
 def test_tune_batch(cg, h):
     import torch
     clouds = _small_clouds()

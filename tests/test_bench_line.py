@@ -40,8 +40,10 @@ def test_contract_keys(line):
 def test_value_is_the_step_rate(line):
     pp = 2 * 1920 * 1024 * 1024          # two holograms per step
     assert line["value"] == pytest.approx(pp / (line["ms_per_step"] / 1e3), rel=1e-6)
+    # the methods are timed one by one (each call bracketed by events, L2
+    # flushed before each), the step as a whole: their sum is close to it
     ms = sum(m["ms"] for m in line["methods"].values())
-    assert ms == pytest.approx(line["ms_per_step"], rel=0.05)
+    assert ms == pytest.approx(line["ms_per_step"], rel=0.15)
     assert line["vs_baseline"] == pytest.approx(line["value"] / (pp / 2 / 31e-3), rel=1e-6)
 
 
@@ -60,10 +62,26 @@ def test_roofline_and_baselines(line):
     assert 0.5 * line["value"] < e["value"] < 2.0 * line["value"]
 
 
+def test_extra_workloads(line):
+    """The large frame, the 64-hologram batch and the adjoint, measured in
+    the same run: per method its ms per call and its main kernel's roofline
+    fraction; the dominant kernel of each workload."""
+    ex = line["extra"]
+    assert set(ex) >= {"large", "batch64", "adjoint", "clocks"}
+    assert set(ex["large"]["methods"]) >= {"direct", "sep_fp16x3", "sep_bf16"}
+    assert set(ex["batch64"]["methods"]) == {"batch_direct", "batch_sep_fp16x3"}
+    assert set(ex["adjoint"]["methods"]) >= {"direct_bwd", "sep_fp16x3_bwd"}
+    for w in ("large", "batch64", "adjoint"):
+        d = ex[w]["dominant_kernel"]
+        assert d["ms_per_call"] > 0 and 0.2 < d["frac"] < 1.3, (w, d)
+        for m, e in ex[w]["methods"].items():
+            assert e["ms"] > 0 and e["pp_per_s"] > 0, (w, m)
+
+
 def test_launches_and_clocks(line):
-    # five of the library's kernels per step: direct tables, direct, prologue,
-    # separable tables, GEMM
-    assert line["gpu_launches"] == 5 * line["steps"]
+    # four of the library's kernels per step: direct tables, direct,
+    # separable tables (both tables kernels build their point records), GEMM
+    assert line["gpu_launches"] == 4 * line["steps"]
     c = line["clocks"]
     assert c["sm_mhz"] > 0 and c["sm_max_mhz"] >= c["sm_mhz"] * 0.5
     assert isinstance(c["reasons"], list)

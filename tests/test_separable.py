@@ -118,4 +118,5 @@ def test_empty_and_launch_count(cg, h):
                    p=8e-6)
     n0 = cg.cgh_launch_count(h)
     _fwd(cg, h, c, "sep_fp16x3")
-    assert cg.cgh_launch_count(h) - n0 == 3   # prologue, tables, GEMM
+    # tables (building the point records themselves), GEMM
+    assert cg.cgh_launch_count(h) - n0 == 2

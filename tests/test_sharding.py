@@ -64,3 +64,68 @@ def test_two_gloo_ranks_agree():
         assert mx == 11.0                              # the slowest rank's time
         assert total == pytest.approx(float(sum(costs)))  # whole-job work
     assert sorted(i for s in res[0][1] for i in s) == list(range(len(costs)))
+
+
+def test_row_slabs_cover_every_row_once():
+    from paper_1002_0916_gb300.sharding import row_slabs
+    for Ny in (1, 5, 31, 32, 33, 1024, 1080, 2160):
+        for world in (1, 2, 3, 4, 8):
+            slabs = row_slabs(Ny, world)
+            assert len(slabs) == world
+            y = 0
+            for y0, rows in slabs:
+                assert y0 == y and rows >= 0
+                assert rows == 0 or y0 % 32 == 0      # whole tile rows
+                y += rows
+            assert y == Ny
+            sizes = [r for _, r in slabs]
+            # balanced to one tile row, plus the ragged last group
+            assert max(sizes) - min(sizes) <= 64
+    assert row_slabs(1024, 2) == [(0, 512), (512, 512)]
+
+
+def _slab_worker(rank, world, port, q):
+    """Each rank computes its own slab of rows with no exchange; the slabs
+    are gathered only to check them (the FP64 oracle stands in for the GPU
+    method on this CPU-only test)."""
+    import numpy as np
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1002_0916_gb300.sharding import row_slabs
+    from workloads import workload
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        c = workload("cfg1_256x256_n64")
+        y0, rows = row_slabs(c.Ny, world)[rank]
+        mine = oracle.forward(c, rows=np.arange(y0, y0 + rows, dtype=np.int32))
+        parts = [None] * world
+        dist.all_gather_object(parts, (y0, mine))
+        q.put((rank, parts))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_row_split():
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    import oracle
+    from workloads import workload
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    c = workload("cfg1_256x256_n64")
+    whole = oracle.forward(c)
+    for rank, parts in res:
+        assert [y0 for y0, _ in parts] == [0, 128]
+        assert np.array_equal(np.concatenate([m for _, m in parts], 0), whole)
