@@ -424,7 +424,10 @@ cgh_status cgh_set_direct_tile(cgh_handle h, const cgh_direct_tile *tile);
  * tiles) and remember the fastest for the size bucket; later calls of that
  * method and size on this handle use it while the GEMM tiling is
  * CGH_GEMM_AUTO (read it back with cgh_gemm_plan_for); *chosen, if not NULL,
- * is zeroed.  Choices are kept in the handle and, if the environment
+ * is zeroed.  Every candidate is timed in three rounds over all of them
+ * (a warm-up call and three timed calls each, its fastest call counting);
+ * the built-in heuristic's choice is kept unless another candidate is more
+ * than 1% faster.  Choices are kept in the handle and, if the environment
  * variable CGH_TUNE_CACHE names a file, appended there as one JSON object
  * per line (device name, size bucket, tile or GEMM plan) and read back by
  * later handles.  Other methods: CGH_ERR_UNSUPPORTED. */
@@ -474,8 +477,10 @@ cgh_status cgh_kernel_time(cgh_handle h, int kernel, double *total_ms,
  * NULL).  CGH_SEP_FP16X3: time the persistent grouped GEMM's two item
  * shapes (one-CTA 128 x 128 items and CTA-pair 256 x 128 items) and keep
  * the faster for batches of the same sizes (*chosen, if not NULL, is
- * zeroed).  Later cgh_batch calls of that method and these sizes use the
- * choice (with the GEMM tiling CGH_GEMM_AUTO for the separable batch);
+ * zeroed).  The built-in choice (the heuristic's tile; one-CTA items) is
+ * kept unless another is more than 1% faster.  Later cgh_batch calls of
+ * that method and these sizes use the choice (with the GEMM tiling
+ * CGH_GEMM_AUTO for the separable batch);
  * cgh_batch_plan reports it.  Errors as cgh_batch. */
 cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs, int count,
                           int method, void *stream, cgh_direct_tile *chosen);

@@ -167,6 +167,13 @@ struct cgh_ctx {
 
 // autotune.cu
 std::string size_bucket(int method, int N, int Nx, int Ny);
+// The measuring loop of the tuners: the fastest of n candidates (run(i)
+// enqueues one call of candidate i), keeping candidate dflt unless another
+// beats it by more than the fraction `keep`.
+cgh_status tune_pick(cgh_ctx *h, int n, int dflt, double keep, cudaStream_t s,
+                     const std::function<cgh_status(int)> &run, int *best, float *best_ms,
+                     int rounds = 3, int calls = 3);
+constexpr double TUNE_KEEP = 0.01;
 // batch.cu: tuning-cache key of a batch geometry (sizes only)
 std::string batch_bucket(const cgh_problem *probs, int count);
 int default_direct_tile(int N, int Nx, int Ny, int sm_count);

@@ -12,7 +12,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <string>
+#include <vector>
 
 #include "api_internal.h"
 #include "common.cuh"
@@ -78,6 +80,50 @@ static const char *cache_path() {
     return (p && *p) ? p : nullptr;
 }
 
+// Time n candidates, run(i) enqueueing one call of candidate i on s: `rounds`
+// rounds over all candidates, each a warm-up call and `calls` timed calls
+// (CUDA events), so that slow drifts of the clock touch every candidate
+// alike; a candidate's time is its fastest call.  *best: the fastest candidate --
+// unless the default candidate dflt is within a factor (1 + keep) of it, in
+// which case the default stays: a tuned shape must beat the built-in
+// choice by a clear margin, not by noise.
+cgh_status tune_pick(cgh_ctx *h, int n, int dflt, double keep, cudaStream_t s,
+                     const std::function<cgh_status(int)> &run, int *best, float *best_ms,
+                     int rounds, int calls) {
+    std::vector<float> t(n, 1e30f);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    cgh_status st = ce == cudaSuccess ? CGH_OK : h->cuda_fail(ce, "tuning events");
+    for (int round = 0; round < rounds && st == CGH_OK; ++round) {
+        for (int i = 0; i < n && st == CGH_OK; ++i) {
+            st = run(i);
+            for (int r = 0; r < calls && st == CGH_OK; ++r) {
+                cudaEventRecord(e0, s);
+                st = run(i);
+                cudaEventRecord(e1, s);
+                if (st) break;
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t[i] = std::min(t[i], ms);
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return h->cuda_fail(e, "tuning");
+    int b = 0;
+    for (int i = 1; i < n; ++i)
+        if (t[i] < t[b]) b = i;
+    if (dflt >= 0 && dflt < n && t[dflt] <= t[b] * (1.0 + keep)) b = dflt;
+    *best = b;
+    if (best_ms) *best_ms = t[b];
+    return CGH_OK;
+}
+
 void cgh_ctx::load_tune_cache() {
     const char *path = cache_path();
     if (!path) return;
@@ -124,45 +170,30 @@ static cgh_status tune_separable(cgh_ctx *h, int N, int Nx, int Ny, int method,
                                  const float *z, float *out) {
     const int kind = method == CGH_SEP_BF16 ? 0 : method == CGH_SEP_FP16 ? 1 : 2;
     static const int widths[] = {112, 128, 144, 160, 224, 256};
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best_ms = 1e30f;
-    int best = -1;
-    cgh_status st = CGH_OK;
-    for (int tiling = CGH_GEMM_SINGLE; tiling <= CGH_GEMM_PAIRS_GEN && st == CGH_OK;
-         ++tiling) {
+    std::vector<int> plans;
+    for (int tiling = CGH_GEMM_SINGLE; tiling <= CGH_GEMM_PAIRS_GEN; ++tiling)
         for (int w : widths) {
             const bool ok = tiling == CGH_GEMM_SINGLE ? (w == 112 || w == 128)
                             : tiling == CGH_GEMM_PAIRS ? pair_width_ok(w)
                                                        : gen_pair_width_ok(kind, w);
-            if (!ok) continue;
-            h->forced_plan = tiling * 1000 + w;
-            st = h->forward_separable(pts, A, z, N, 532e-9, 8e-6, Nx, Ny, out, method, s);
-            float ms_i = 1e30f;
-            for (int r = 0; r < 3 && st == CGH_OK; ++r) {
-                cudaEventRecord(e0, s);
-                st = h->forward_separable(pts, A, z, N, 532e-9, 8e-6, Nx, Ny, out,
-                                          method, s);
-                cudaEventRecord(e1, s);
-                if (st) break;
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms_i = ms < ms_i ? ms : ms_i;
-            }
-            if (st) break;
-            if (ms_i < best_ms) {
-                best_ms = ms_i;
-                best = h->forced_plan;
-            }
+            if (ok) plans.push_back(tiling * 1000 + w);
         }
-    }
+    // the heuristic's plan is the default
+    const GemmPlan hp = gemm_plan(Ny, Nx, CGH_GEMM_AUTO, h->sm_count, kind);
+    int dflt = -1;
+    for (size_t i = 0; i < plans.size(); ++i)
+        if (plans[i] == hp.tiling * 1000 + hp.bn) dflt = (int)i;
+    int bi = -1;
+    float best_ms = 0.0f;
+    cgh_status st = tune_pick(h, (int)plans.size(), dflt, TUNE_KEEP, s,
+                              [&](int i) {
+                                  h->forced_plan = plans[i];
+                                  return h->forward_separable(pts, A, z, N, 532e-9, 8e-6,
+                                                              Nx, Ny, out, method, s);
+                              },
+                              &bi, &best_ms);
     h->forced_plan = -1;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaError_t e = cudaGetLastError();
-    if (st == CGH_OK && e != cudaSuccess) st = h->cuda_fail(e, "tuning");
+    const int best = (st == CGH_OK && bi >= 0) ? plans[bi] : -1;
     if (st == CGH_OK && best >= 0) {
         const std::string b = size_bucket(method, N, Nx, Ny);
         h->tuned_gemm[b] = best;
@@ -216,36 +247,15 @@ extern "C" cgh_status cgh_tune(cgh_handle h, int N, int Nx, int Ny, int method,
         cudaSetDevice(prev_dev);
         return st;
     }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best_ms = 1e30f;
+    float best_ms = 0.0f;
     int best_i = -1;
-    for (int i = 0; i < direct_tile_count(); ++i) {
-        // one warm-up, then the best of three
-        st = h->forward_direct(pts, A, z, N, 532e-9, 8e-6, Nx, Ny, out, i, s);
-        if (st) break;
-        float ms_i = 1e30f;
-        for (int r = 0; r < 3; ++r) {
-            cudaEventRecord(e0, s);
-            st = h->forward_direct(pts, A, z, N, 532e-9, 8e-6, Nx, Ny, out, i, s);
-            cudaEventRecord(e1, s);
-            if (st) break;
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < ms_i) ms_i = ms;
-        }
-        if (st) break;
-        if (ms_i < best_ms) {
-            best_ms = ms_i;
-            best_i = i;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaError_t e = cudaGetLastError();
-    if (st == CGH_OK && e != cudaSuccess) st = h->cuda_fail(e, "tuning");
+    st = tune_pick(h, direct_tile_count(), default_direct_tile(N, Nx, Ny, h->sm_count),
+                   TUNE_KEEP, s,
+                   [&](int i) {
+                       return h->forward_direct(pts, A, z, N, 532e-9, 8e-6, Nx, Ny, out,
+                                                i, s);
+                   },
+                   &best_i, &best_ms);
     if (st == CGH_OK && best_i >= 0) {
         std::string b = size_bucket(CGH_DIRECT_FP32, N, Nx, Ny);
         h->tuned[b] = best_i;

@@ -490,34 +490,14 @@ extern "C" cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs,
     if (prev != h->device) cudaSetDevice(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (method == CGH_SEP_FP16X3) {
-        // the grouped split-FP16 GEMM's two item shapes: one-CTA items and
-        // CTA-pair items (each timed on its captured graph, best of three)
-        cgh_status st = CGH_OK;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        float best = 1e30f;
+        // the grouped split-FP16 GEMM's two item shapes: one-CTA items (the
+        // default) and CTA-pair items, each timed on its captured graph
         int best_pairs = -1;
-        for (int pairs = 0; pairs < 2 && st == CGH_OK; ++pairs) {
-            st = h->batch(probs, count, method, s, -1, pairs);  // builds the graph
-            float ms_p = 1e30f;
-            for (int r = 0; r < 3 && st == CGH_OK; ++r) {
-                cudaEventRecord(e0, s);
-                st = h->batch(probs, count, method, s, -1, pairs);
-                cudaEventRecord(e1, s);
-                if (st) break;
-                cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms_p = ms < ms_p ? ms : ms_p;
-            }
-            if (st == CGH_OK && ms_p < best) {
-                best = ms_p;
-                best_pairs = pairs;
-            }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        cgh_status st = tune_pick(h, 2, 0, TUNE_KEEP, s,
+                                  [&](int pairs) {
+                                      return h->batch(probs, count, method, s, -1, pairs);
+                                  },
+                                  &best_pairs, nullptr);
         if (st == CGH_OK && best_pairs >= 0)
             h->tuned_gemm[batch_bucket(probs, count) + "_sep"] =
                 (best_pairs ? CGH_GEMM_PAIRS : CGH_GEMM_SINGLE) * 1000 +
@@ -526,29 +506,13 @@ extern "C" cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs,
         if (prev != h->device) cudaSetDevice(prev);
         return st;
     }
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
     int best_i = -1;
-    cgh_status st = CGH_OK;
-    for (int i = 0; i < direct_tile_count() && st == CGH_OK; ++i) {
-        st = h->batch(probs, count, CGH_DIRECT_FP32, s, i);  // builds the graph
-        if (st) break;
-        cudaEventRecord(e0, s);
-        st = h->batch(probs, count, CGH_DIRECT_FP32, s, i);
-        cudaEventRecord(e1, s);
-        if (st) break;
-        cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_i = i;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cgh_status st = tune_pick(h, direct_tile_count(), h->default_batch_tile(probs, count),
+                              TUNE_KEEP, s,
+                              [&](int i) {
+                                  return h->batch(probs, count, CGH_DIRECT_FP32, s, i);
+                              },
+                              &best_i, nullptr, 1, 2);  // (each call is a whole batch)
     if (st == CGH_OK && best_i >= 0) {
         h->tuned[batch_bucket(probs, count)] = best_i;
         if (chosen) {

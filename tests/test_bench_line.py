@@ -21,7 +21,7 @@ def line():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "3",
-                        "--warmup", "3"], capture_output=True, text=True, timeout=900,
+                        "--warmup", "3"], capture_output=True, text=True, timeout=400,
                        cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     return json.loads(r.stdout.strip().splitlines()[-1])
