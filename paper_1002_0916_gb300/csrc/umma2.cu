@@ -167,6 +167,13 @@ umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
         if (MODE == 1 && ok && !abort_flag) {
             adjoint_epilogue<BNP, SPLIT, S::ACC1>(tmem + ((uint32_t)(q * 32) << 16), row,
                                                   np0, g, ea, lane, blockIdx.x >> 1);
+        } else if (ok && !abort_flag && g.by_lines) {
+            // (the stage ring is idle: every MMA, hence every operand read,
+            // has completed)
+            const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
+            epilogue_rows_by_lines<BNP, SPLIT, S::ACC1>(
+                tmem + ((uint32_t)(q * 32) << 16), m0 + q * 32, np0, g,
+                reinterpret_cast<float *>(smem + q * 4096), lane, vec);
         } else if (ok && !abort_flag) {
             const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
             float *drow = g.D + (long long)row * g.ldd;
@@ -235,10 +242,21 @@ static cudaError_t launch_pair_t(const GemmOperands &op, unsigned *status,
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status, op.accumulate};
+    g.by_lines = MODE == 0 && !epilogue_plain_stores() ? 1 : 0;
     dim3 grid(2 * ((op.N + BNP - 1) / BNP), (op.M + 2 * S::BM - 1) / (2 * S::BM));
     const uint32_t idesc = umma::idesc_f16(2 * S::BM, BNP, op.bf16);
     return launch_dependent(kern, grid, dim3(192), S::SMEM, s, tA, tB, tA2, tB2, g, ea,
                             idesc);
+}
+
+// CGH_GEMM_PLAIN_EPILOGUE=1: the forward pair GEMMs store D row by row from
+// registers instead of through shared memory (for measuring the difference).
+bool epilogue_plain_stores() {
+    static const bool plain = [] {
+        const char *f = getenv("CGH_GEMM_PLAIN_EPILOGUE");
+        return f && atoi(f) != 0;
+    }();
+    return plain;
 }
 
 // The pair widths compiled in (columns of one 256-row pair tile).

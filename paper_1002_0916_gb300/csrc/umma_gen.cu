@@ -245,7 +245,14 @@ umma_gen_pair_kernel(GenArgs ga, GemmArgs g, uint32_t idesc) {
             umma::fence_after_sync();
             pdl_trigger();  // only the epilogue is left
             if (!ok) set_status(g.status, DEV_TIMEOUT);
-            if (ok && !abort_flag) {
+            if (ok && !abort_flag && g.by_lines) {
+                // (every MMA has completed and every producer has written its
+                // last stage: the stage ring is idle)
+                const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
+                epilogue_rows_by_lines<BNP, SPLIT, S::ACC1>(
+                    tmem + ((uint32_t)(qq * 32) << 16), m0 + qq * 32, np0, g,
+                    reinterpret_cast<float *>(smem + qq * 4096), lane, vec);
+            } else if (ok && !abort_flag) {
                 const uint32_t t_row = tmem + ((uint32_t)(qq * 32) << 16);
                 float *drow = g.D + (long long)row * g.ldd;
                 const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
@@ -357,6 +364,7 @@ cudaError_t launch_umma_gen(const PointRec *rec, int N, int Npad, int kind, int 
         const int j0 = k0 / 2;
         GenArgs ga{rec + j0, N - j0};
         GemmArgs g{M, Ncols, Kc, D, ldd, lo_scale, status, k0 > 0 ? 1 : 0};
+        g.by_lines = epilogue_plain_stores() ? 0 : 1;
         cudaError_t e = launch_gen_one(ga, g, kind, bnp, s);
         if (e != cudaSuccess) return e;
     }

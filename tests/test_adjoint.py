@@ -5,6 +5,8 @@ Bound: relative error ||g - g_ref|| / ||g_ref|| <= 1e-3 per parameter group
 (A, x, y, z); finite differences per sampled component:
 |g - fd| <= 1e-3 max(|fd|, rms(fd of that group))."""
 import functools
+import json
+import os
 
 import numpy as np
 import pytest
@@ -51,13 +53,18 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def _check_groups(got, ref, sel=None):
+def _check_groups(got, ref, sel=None, log=None):
     gp, gA, gz = got
     rp, rA, rz = ref
     if sel is not None:
         gp, gA, gz = gp[sel], gA[sel], gz[sel]
     errs = {"A": _rel(gA, rA), "x": _rel(gp[:, 0], rp[:, 0]),
             "y": _rel(gp[:, 1], rp[:, 1]), "z": _rel(gz, rz)}
+    path = os.environ.get("CGH_ACCURACY_LOG")
+    if path and log is not None:
+        with open(path, "a") as fh:
+            fh.write(json.dumps({"workload": log[0], "method": log[1], "points": int(
+                len(gA)), "grad_rel": errs}) + "\n")
     assert all(v <= TOL for v in errs.values()), errs
     return errs
 
@@ -97,7 +104,7 @@ def test_cfg5_full_size_sampled_points(cg, h, method):
     G = grad_field(11, c.Nx, c.Ny, scale=40.0)
     got = _bwd(cg, h, c, G, method)
     sel, ref = _cfg5_grad_ref()
-    _check_groups(got, ref, sel)
+    _check_groups(got, ref, sel, log=(c.name, method))
 
 
 @functools.lru_cache(maxsize=None)
