@@ -261,7 +261,6 @@ inline int gemm_k_chunks(int K, bool split) {
 // The pair tile width for an M x N product and its cost (SM waves x width).
 int pick_pair_n(int M, int N, int sms, double *cost = nullptr);
 bool pair_width_ok(int bnp);
-bool epilogue_plain_stores();
 // How launch_umma_gemm tiles an M x N forward product under a cgh_gemm_tiles
 // setting: CGH_GEMM_SINGLE or CGH_GEMM_PAIRS, and the tile width.
 struct GemmPlan {

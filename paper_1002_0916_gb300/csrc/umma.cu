@@ -127,6 +127,14 @@ umma_gemm_kernel(const __grid_constant__ CUtensorMap tA,
             // let this CTA's own copies land before its shared memory goes
             for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
                 mbar_wait_bounded(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
+        } else {
+            // The MMA issuer's commits of the last stages arrive on this
+            // CTA's empty barriers asynchronously, and nothing else waits for
+            // them: wait here (bounded), so that no arrive is still in flight
+            // when the CTA exits and its shared memory passes to the next CTA
+            // on the SM.
+            for (int kb = KB - STAGES < 0 ? 0 : KB - STAGES; kb < KB; ++kb)
+                mbar_wait_bounded(&empty[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
         }
     } else if (warp == 1 && lane == 0) {
         // --------------------------------------------------- MMA issuer
@@ -480,6 +488,15 @@ umma_grouped_kernel(const GroupProb *__restrict__ probs,
             unsigned lo = issued_from > STAGES ? issued_from - STAGES : 0;
             for (unsigned u = lo; u < issued_from; ++u)
                 mbar_wait_bounded(&full[u % STAGES], (uint32_t)((u / STAGES) & 1));
+        } else {
+            // The MMA issuer's commits of the last stages arrive on this
+            // CTA's empty barriers asynchronously, and nothing else waits for
+            // them: wait here (bounded), so that no arrive is still in flight
+            // when the CTA exits and its shared memory passes to the next CTA
+            // on the SM.
+            const unsigned lo = g > STAGES ? g - STAGES : 0;
+            for (unsigned u = lo; u < g; ++u)
+                mbar_wait_bounded(&empty[u % STAGES], (uint32_t)((u / STAGES) & 1));
         }
     } else if (warp == 1 && lane == 0) {
         // --------------------------------------------------- MMA issuer

@@ -115,6 +115,14 @@ umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
             // completion; it leaves only after the closing cluster barrier)
             for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
                 mbar_wait_bounded(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
+        } else if (!abort_flag) {
+            // The MMA issuer's commits of the last stages arrive on this
+            // CTA's empty barriers asynchronously (multicast to both CTAs),
+            // and nothing else waits for them: wait here (bounded), so that
+            // no arrive is still in flight when the CTA exits and its shared
+            // memory passes to the next CTA on the SM.
+            for (int kb = KB - STAGES < 0 ? 0 : KB - STAGES; kb < KB; ++kb)
+                mbar_wait_bounded(&empty[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
         }
     } else if (warp == 1 && lane == 0) {
         if (rank == 0) {
@@ -167,13 +175,6 @@ umma_pair_kernel(const __grid_constant__ CUtensorMap tA,
         if (MODE == 1 && ok && !abort_flag) {
             adjoint_epilogue<BNP, SPLIT, S::ACC1>(tmem + ((uint32_t)(q * 32) << 16), row,
                                                   np0, g, ea, lane, blockIdx.x >> 1);
-        } else if (ok && !abort_flag && g.by_lines) {
-            // (the stage ring is idle: every MMA, hence every operand read,
-            // has completed)
-            const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
-            epilogue_rows_by_lines<BNP, SPLIT, S::ACC1>(
-                tmem + ((uint32_t)(q * 32) << 16), m0 + q * 32, np0, g,
-                reinterpret_cast<float *>(smem + q * 4096), lane, vec);
         } else if (ok && !abort_flag) {
             const uint32_t t_row = tmem + ((uint32_t)(q * 32) << 16);
             float *drow = g.D + (long long)row * g.ldd;
@@ -242,21 +243,10 @@ static cudaError_t launch_pair_t(const GemmOperands &op, unsigned *status,
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     GemmArgs g{op.M, op.N, op.K, op.D, op.ldd, op.lo_scale, status, op.accumulate};
-    g.by_lines = MODE == 0 && !epilogue_plain_stores() ? 1 : 0;
     dim3 grid(2 * ((op.N + BNP - 1) / BNP), (op.M + 2 * S::BM - 1) / (2 * S::BM));
     const uint32_t idesc = umma::idesc_f16(2 * S::BM, BNP, op.bf16);
     return launch_dependent(kern, grid, dim3(192), S::SMEM, s, tA, tB, tA2, tB2, g, ea,
                             idesc);
-}
-
-// CGH_GEMM_PLAIN_EPILOGUE=1: the forward pair GEMMs store D row by row from
-// registers instead of through shared memory (for measuring the difference).
-bool epilogue_plain_stores() {
-    static const bool plain = [] {
-        const char *f = getenv("CGH_GEMM_PLAIN_EPILOGUE");
-        return f && atoi(f) != 0;
-    }();
-    return plain;
 }
 
 // The pair widths compiled in (columns of one 256-row pair tile).
@@ -404,6 +394,15 @@ umma_grouped_pair_kernel(const GroupProb *__restrict__ probs,
             const unsigned lo = issued_from > STAGES ? issued_from - STAGES : 0;
             for (unsigned u = lo; u < issued_from; ++u)
                 mbar_wait_bounded(&full[u % STAGES], (uint32_t)((u / STAGES) & 1));
+        } else if (!abort_flag) {
+            // The MMA issuer's commits of the last stages arrive on this
+            // CTA's empty barriers asynchronously (multicast to both CTAs),
+            // and nothing else waits for them: wait here (bounded), so that
+            // no arrive is still in flight when the CTA exits and its shared
+            // memory passes to the next CTA on the SM.
+            const unsigned lo = g > STAGES ? g - STAGES : 0;
+            for (unsigned u = lo; u < g; ++u)
+                mbar_wait_bounded(&empty[u % STAGES], (uint32_t)((u / STAGES) & 1));
         }
     } else if (warp == 1 && lane == 0 && rank == 0) {
         // ---------------------------------------- MMA issuer (even CTA)

@@ -15,7 +15,6 @@ struct GemmArgs {
     float lo_scale;
     unsigned *status;
     int accumulate;  // 0: D = product; 1: D += product (a later K chunk)
-    int by_lines = 0;  // 1: the forward epilogue stores through shared memory
 };
 
 // Store CH consecutive FP32 values of one output row (row < M checked by the
@@ -52,94 +51,6 @@ __device__ __forceinline__ void epilogue_store_row(float *drow, int col, float (
 #pragma unroll
         for (int i = 0; i < CH; ++i)
             if (col + i < g.N) drow[col + i] = g.accumulate ? drow[col + i] + v[i] : v[i];
-    }
-}
-
-// Epilogue of one warp's 32 accumulator rows (TMEM lane quarter at t_row,
-// output rows row0 .. row0 + 31, columns col0 .. col0 + BN - 1) through
-// shared memory (`buf`: 32 x W floats, W = 32 when BN allows, else 16): per
-// W columns every lane writes its row's W values (its 16-byte chunks
-// rotated by the row, so that each 8-lane phase of the warp's stores hits
-// 32 distinct banks), then reads back so that W / 4 lanes hold one row's
-// 4 W contiguous bytes: each warp store instruction then covers 128 / W
-// rows of 4 W bytes instead of 32 rows of 16 bytes (32 cache lines).  With
-// g.accumulate the lane first loads all the D values it will add to, then
-// adds (FP32, round to nearest, as epilogue_store_row) and stores.
-template <int BN, bool SPLIT, uint32_t ACC1>
-__device__ __forceinline__ void epilogue_rows_by_lines(uint32_t t_row, int row0, int col0,
-                                                       const GemmArgs &g, float *buf,
-                                                       int lane, bool vec) {
-    constexpr int W = BN % 32 == 0 ? 32 : 16;  // columns per piece
-    constexpr int CPR = W / 4;                 // 16-byte chunks per row
-    constexpr int RPI = 32 / CPR;              // rows per read-back instruction
-    constexpr int NJ = 32 / RPI;               // read-back instructions
-    static_assert(BN % 16 == 0, "16-column pieces");
-    const int rsel = lane / CPR, k = lane % CPR;  // read-back: row (of RPI), chunk
-#pragma unroll 1
-    for (int c = 0; c < BN; c += W) {
-        uint32_t r[W];
-        float v[W];
-        if constexpr (W == 32) umma::tmem_ld32(t_row + c, r);
-        else umma::tmem_ld16(t_row + c, r);
-        if (SPLIT) {
-            uint32_t r2[W];
-            if constexpr (W == 32) umma::tmem_ld32(t_row + ACC1 + c, r2);
-            else umma::tmem_ld16(t_row + ACC1 + c, r2);
-            umma::tmem_ld_wait();
-#pragma unroll
-            for (int i = 0; i < W; ++i)
-                v[i] = fmaf(g.lo_scale, __uint_as_float(r2[i]), __uint_as_float(r[i]));
-        } else {
-            umma::tmem_ld_wait();
-#pragma unroll
-            for (int i = 0; i < W; ++i) v[i] = __uint_as_float(r[i]);
-        }
-        // row `lane`: chunk q at q ^ rot (W = 32: rot = lane mod 8; W = 16,
-        // rows of 64 bytes, two per 128 bytes: rot = (lane / 2) mod 4)
-        const int rot = W == 32 ? (lane & 7) : ((lane >> 1) & 3);
-#pragma unroll
-        for (int q = 0; q < CPR; ++q)
-            *reinterpret_cast<float4 *>(buf + lane * W + ((q ^ rot) << 2)) =
-                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        __syncwarp();
-        const int col = col0 + c + 4 * k;
-        float4 w[NJ];
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int rr = rsel + RPI * j;  // row of the warp's 32
-            const int rrot = W == 32 ? (rr & 7) : ((rr >> 1) & 3);
-            w[j] = *reinterpret_cast<const float4 *>(buf + rr * W + ((k ^ rrot) << 2));
-        }
-        __syncwarp();  // every lane has read the buffer before the next piece
-        const bool full = vec && col + 4 <= g.N;
-        if (g.accumulate && full) {
-            float4 old[NJ];
-#pragma unroll
-            for (int j = 0; j < NJ; ++j) {
-                const int row = row0 + rsel + RPI * j;
-                old[j] = row < g.M ? *reinterpret_cast<const float4 *>(
-                                         g.D + (long long)row * g.ldd + col)
-                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int j = 0; j < NJ; ++j)
-                w[j] = make_float4(old[j].x + w[j].x, old[j].y + w[j].y, old[j].z + w[j].z,
-                                   old[j].w + w[j].w);
-        }
-#pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int row = row0 + rsel + RPI * j;
-            if (row >= g.M) continue;
-            float *d = g.D + (long long)row * g.ldd + col;
-            if (full) {
-                *reinterpret_cast<float4 *>(d) = w[j];
-            } else {
-                const float e[4] = {w[j].x, w[j].y, w[j].z, w[j].w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (col + i < g.N) d[i] = g.accumulate ? d[i] + e[i] : e[i];
-            }
-        }
     }
 }
 

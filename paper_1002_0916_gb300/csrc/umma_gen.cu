@@ -236,6 +236,15 @@ umma_gen_pair_kernel(GenArgs ga, GemmArgs g, uint32_t idesc) {
             __syncwarp();
             if (lane == 0) umma2::remote_arrive(full_even0 + (uint32_t)s * 8u);
         }
+        if (warp == GEN_PRODUCER_WARPS && lane == 0 && !abort_flag) {
+            // The MMA issuer's commits of the last stages arrive on this
+            // CTA's empty barriers asynchronously (multicast to both CTAs),
+            // and nothing else waits for them: wait here (bounded), so that
+            // no arrive is still in flight when the CTA exits and its shared
+            // memory passes to the next CTA on the SM.
+            for (int kb = KB - STAGES < 0 ? 0 : KB - STAGES; kb < KB; ++kb)
+                mbar_wait_bounded(&empty[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
+        }
         // ------------------------------------ epilogue (warps 1-4, both CTAs)
         if (warp <= 4) {
             const int qq = warp & 3;  // the 32-lane quarter of TMEM this warp reads
@@ -245,14 +254,7 @@ umma_gen_pair_kernel(GenArgs ga, GemmArgs g, uint32_t idesc) {
             umma::fence_after_sync();
             pdl_trigger();  // only the epilogue is left
             if (!ok) set_status(g.status, DEV_TIMEOUT);
-            if (ok && !abort_flag && g.by_lines) {
-                // (every MMA has completed and every producer has written its
-                // last stage: the stage ring is idle)
-                const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
-                epilogue_rows_by_lines<BNP, SPLIT, S::ACC1>(
-                    tmem + ((uint32_t)(qq * 32) << 16), m0 + qq * 32, np0, g,
-                    reinterpret_cast<float *>(smem + qq * 4096), lane, vec);
-            } else if (ok && !abort_flag) {
+            if (ok && !abort_flag) {
                 const uint32_t t_row = tmem + ((uint32_t)(qq * 32) << 16);
                 float *drow = g.D + (long long)row * g.ldd;
                 const bool vec = ((g.ldd & 3) == 0) && ((((uintptr_t)g.D) & 15) == 0);
@@ -364,7 +366,6 @@ cudaError_t launch_umma_gen(const PointRec *rec, int N, int Npad, int kind, int 
         const int j0 = k0 / 2;
         GenArgs ga{rec + j0, N - j0};
         GemmArgs g{M, Ncols, Kc, D, ldd, lo_scale, status, k0 > 0 ? 1 : 0};
-        g.by_lines = epilogue_plain_stores() ? 0 : 1;
         cudaError_t e = launch_gen_one(ga, g, kind, bnp, s);
         if (e != cudaSuccess) return e;
     }
