@@ -335,6 +335,7 @@ class Leg:
         self.problems = None          # batch legs: the problems (for the tuner)
         self.plan = None              # batch legs: what cgh_batch runs
         self.size = None              # forward legs: (N, Nx, Ny) of one call
+        self.tile = None              # direct and batch legs: the direct tile used
 
 
 # kernel (cgh_kernel_id name) that carries a forward method's point-pixel work
@@ -444,7 +445,8 @@ def build_legs(cg, h, which, methods, dev, stream, shard=None):
                 stream=stream))
             mult = 3.0 if m == "sep_fp16x3" else 0.0
             legs.append(Leg(m + "_fwd", f_fwd, c.pp, 4.0 * c.pp * mult, 1 if mult else 0,
-                            kernel=MAIN_KERNEL[m]))
+                            kernel=MAIN_KERNEL[m], method=m))
+            legs[-1].size = (c.N, c.Nx, c.Ny)
             legs.append(Leg(m + "_bwd", f_bwd, c.pp, 2 * 4.0 * c.pp * mult,
                             2 if mult else 0,
                             kernel={"direct": "bwd_direct", "sep_fp32": "bwd_simt"}.get(
@@ -457,10 +459,29 @@ ALU_KERNELS = ("direct", "naive", "batch", "bwd_direct", "recur", "simt", "bwd_s
 GEMM_KERNELS = ("gemm", "bwd_gemm", "batch_sep")
 
 
-def alu_recipe(kernel):
+def alu_recipe(kernel, tile=None):
     """(updates per clk per SM at the nominal pipe rates, description, the
     same bound as a function of the measured rates (m MUFU cosines, f FP32
-    multiply-adds per clk per SM), MUFU operations per update)."""
+    multiply-adds per clk per SM), MUFU operations per update).  tile: the
+    direct tile shape a direct or batch kernel ran with (its recipe)."""
+    pk = tile[7] if tile else None
+    if kernel in ("direct", "batch") and pk is not None and pk >= 7:
+        vx, vy = tile[2], tile[3]
+        # per point and thread: the angle add, the sincos argument scale, 2
+        # amplitude products, 4 per row rotation (VY - 1 rows), and 2 per
+        # pixel (1 for the row's first); the packed form (8) spends 2 on
+        # the first pixel too
+        f = 2.0 + (3.0 if pk == 7 else 4.0) / vx
+        return (128.0 / f,
+                f"FMA-pipe limit of the two-axis rotation recipe ({vx}x{vy} pixels a "
+                f"thread{', packed pixel pairs' if pk == 8 else ''}): {f:.4g} FP32 ops "
+                f"per update, 128 per clk/SM; 2 MUFU ops per {vx * vy} updates",
+                lambda m, fr, f=f: fr / f, 2.0 / (vx * vy))
+    if kernel in ("direct", "batch") and pk == 6:
+        return (32.0,
+                "MUFU limit of the row rotation recipe: a sincos (2 MUFU ops) per "
+                "row of 4 pixels, 16 per clk/SM; 3 FP32 ops per update allow 42.7",
+                lambda m, fr: min(2.0 * m, fr / 3.0), 0.5)
     if kernel == "simt":
         return (SIMT_PP_PER_CLK_PER_SM,
                 "FMA-pipe limit of the FP32 angle-addition product: 2 FP32 "
@@ -487,16 +508,17 @@ def alu_recipe(kernel):
             "updates/clk/SM", lambda m, f: (f + 6.0 * m) / 9.0, 1.0)
 
 
-def kernel_roofline(kernel, pp, flops, ms, sms, peaks, pipe_rates=None, sm_mhz=None):
+def kernel_roofline(kernel, pp, flops, ms, sms, peaks, pipe_rates=None, sm_mhz=None,
+                    tile=None):
     """Roofline of one kernel from its algorithmic work per launch (pp
     point-pixel updates, or flops for a tensor-core GEMM) and its mean launch
-    time in ms."""
+    time in ms; tile: the direct tile shape (direct and batch kernels)."""
     if kernel in ALU_KERNELS and pp:
-        per_clk, src, measured, mufu_per_pp = alu_recipe(kernel)
+        per_clk, src, measured, mufu_per_pp = alu_recipe(kernel, tile)
         achieved = pp / (ms / 1e3) / 1e9
         peak = sms * per_clk * NOMINAL_MAX_MHZ * 1e6 / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Gpp/s", "frac": achieved / peak,
+                "unit": "Gpp/s", "frac": achieved / peak, "tile": list(tile) if tile else None,
                 "peak_source": f"derived: {sms} SMs x {NOMINAL_MAX_MHZ:.0f} MHz max SM "
                                f"clock x {per_clk:.2f} updates/clk/SM ({src})"}
         if pipe_rates:
@@ -547,7 +569,11 @@ def prepare_legs(cg, h, which, methods, dev, stream, shard=None, tune=True):
                 # region; it synchronises)
                 m = leg.method.replace("batch_", "")
                 cg.cgh_tune_batch(h, leg.problems, m, stream=stream)
-                leg.plan = cg.cgh_batch_plan(h, leg.problems, m)
+            if leg.problems:
+                leg.plan = cg.cgh_batch_plan(h, leg.problems, leg.method.replace("batch_", ""))
+                leg.tile = leg.plan["tile"]
+            elif leg.size and leg.kernel == "direct":
+                leg.tile = cg.cgh_direct_tile_for(h, *leg.size)
             leg.fn()
         except cg.CGHError as e:
             if e.status == cg.CGH_ERR_UNSUPPORTED:
@@ -605,8 +631,8 @@ def leg_entries(legs, per_leg, K, sms, peaks, pipe_rates, sm_mhz):
         if k in kt:
             kms = kt[k][0] / K
             roof = kernel_roofline(k, leg.pp, leg.gemm_flops, kms, sms, peaks,
-                                   pipe_rates, sm_mhz)
-            e.update({"kernel": k, "kernel_ms_per_call": kms,
+                                   pipe_rates, sm_mhz, leg.tile)
+            e.update({"kernel": k, "kernel_ms_per_call": kms, "tile": leg.tile,
                       "kernel_launches_per_call": kt[k][1] / K,
                       "kernel_frac": roof["frac"], "kernel_bound": roof["bound"]})
             if "frac_of_measured_rates" in roof:
@@ -633,7 +659,9 @@ def dominant_kernel(legs, per_leg, K):
     pp = statistics.mean(leg.pp for leg in served) if served else None
     flops = statistics.mean(leg.gemm_flops for leg in served) if served else 0.0
     launches = tot[dom][1] / ncalls
-    return dom, dom_ms, pp, flops, launches, {k: v[0] / v[1] for k, v in tot.items()}
+    tile = next((leg.tile for leg in served if leg.tile), None)
+    return (dom, dom_ms, pp, flops, launches, {k: v[0] / v[1] for k, v in tot.items()},
+            tile)
 
 
 EXTRA_WORKLOADS = {
@@ -666,8 +694,8 @@ def measure_extras(cg, h, dev, stream, flush, K, sms, peaks, pipe_rates, gpu_id,
                 leg.fn()
         torch.cuda.synchronize()
         per_leg = time_legs(cg, h, legs, K, flush, stream)
-        dom, dom_ms, pp, flops, nl, _ = dominant_kernel(legs, per_leg, K)
-        roof = kernel_roofline(dom, pp, flops, dom_ms, sms, peaks, pipe_rates)
+        dom, dom_ms, pp, flops, nl, _, tile = dominant_kernel(legs, per_leg, K)
+        roof = kernel_roofline(dom, pp, flops, dom_ms, sms, peaks, pipe_rates, tile=tile)
         e = {"workload": desc, "pp_per_call": {leg.name: leg.pp for leg in legs},
              "methods": leg_entries(legs, per_leg, K, sms, peaks, pipe_rates, None),
              "dominant_kernel": {"kernel": dom, "ms_per_call": dom_ms,
@@ -812,9 +840,10 @@ def run_ours(args):
         value = reduce_sum(pp_step, dist, dev) / (ms / 1e3)
 
     # ---- roofline of the dominant kernel (timed live in timed region 2)
-    dom, dom_ms, pp_dom, flops_dom, nl_dom, kernels_ms = dominant_kernel(legs, per_leg, K)
+    dom, dom_ms, pp_dom, flops_dom, nl_dom, kernels_ms, tile_dom = dominant_kernel(
+        legs, per_leg, K)
     roof = kernel_roofline(dom, pp_dom, flops_dom, dom_ms, sms, peaks, pipe_rates,
-                           clocks.get("sm_mhz") if clocks else None)
+                           clocks.get("sm_mhz") if clocks else None, tile_dom)
     roof["kernel"] = dom
     roof["ms_per_launch"] = dom_ms / max(nl_dom, 1e-9)
     roof["launches_per_call"] = nl_dom

@@ -258,8 +258,10 @@ cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int count,
  *
  * Computes the same hologram as cgh_forward(..., CGH_DIRECT_FP32, ...) on
  * the calling thread's current device, using the same kernels (the tile
- * shape cgh_forward's built-in heuristic picks for the frame, and its
- * default schedule when that schedule's scratch fits), but takes all
+ * shape cgh_forward's built-in heuristic picks for the frame when its
+ * tables fit the array, else the heuristic's best among the shapes whose
+ * tables fit; the default schedule when that schedule's scratch fits too),
+ * but takes all
  * scratch (angle tables, amplitudes, the schedule's partial tiles and
  * counters, status word) from one fixed __device__ array of
  * CGH_NOALLOC_SCRATCH_BYTES.  It calls no cudaMalloc, cudaFree or other
@@ -283,7 +285,7 @@ cgh_status cgh_batch(cgh_handle h, const cgh_problem *probs, int count,
  * Returns CGH_OK; CGH_ERR_INVALID_ARG for the argument errors cgh_forward
  * rejects; CGH_ERR_UNSUPPORTED when the frame needs more scratch than the
  * array holds (about (Nx + Ny) * N * 4 bytes of angle tables plus 4 bytes
- * per point, with Nx, Ny rounded up to 64 and N to 32) -- nothing is
+ * per point, with Nx, Ny rounded up to 64 and N to 64) -- nothing is
  * launched then; CGH_ERR_CUDA if a CUDA call fails. */
 cgh_status cgh_forward_noalloc(const float *points, const float *A,
                                const float *z, int N, double lambda, double p,

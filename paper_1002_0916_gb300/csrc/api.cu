@@ -136,7 +136,7 @@ cgh_status cgh_ctx::forward_direct(const float *points, const float *A,
     char *base = (char *)ws.ptr;
     PointRec *rec = (PointRec *)base;
     float *phx = (float *)(base + rec_b);
-    float *phy = phx + (size_t)nxt * Npad * t.tx;
+    float *phy = phx + direct_x_floats(t, nxt, Npad);
     float *amp = (float *)(base + rec_b + tab_b);
     float *part = nsplit ? (float *)(base + rec_b + tab_b + amp_b) : nullptr;
     unsigned *count =

@@ -177,6 +177,8 @@ constexpr double TUNE_KEEP = 0.01;
 // batch.cu: tuning-cache key of a batch geometry (sizes only)
 std::string batch_bucket(const cgh_problem *probs, int count);
 int default_direct_tile(int N, int Nx, int Ny, int sm_count);
+// autotune.cu: the heuristic's modelled cost of direct tile i for a frame
+double direct_tile_cost(int i, int N, int Nx, int Ny, int sm_count);
 
 // An NVTX range named after a public entry point (and, for the forward
 // calls, the method), open for the life of the call: visible to ncu --nvtx

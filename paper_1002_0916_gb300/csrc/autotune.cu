@@ -30,30 +30,42 @@ std::string size_bucket(int method, int N, int Nx, int Ny) {
     return buf;
 }
 
-int default_direct_tile(int N, int Nx, int Ny, int sm_count) {
+double direct_tile_cost(int i, int N, int Nx, int Ny, int sm_count) {
     (void)N;
+    const DirectTile t = direct_tile_get(i);
+    // CTAs are handed to SMs as earlier ones finish, so an SM's share is
+    // about ceil(CTAs / SMs) CTAs of equal work
+    long long ctas = (long long)((Nx + t.tx - 1) / t.tx) * ((Ny + t.ty - 1) / t.ty);
+    const double waves = (double)((ctas + sm_count - 1) / sm_count);
+    // Per-update cost model (in MUFU-cosine units), from the measured
+    // rates: a quarter of the cosines on the FMA pipe saves about a
+    // sixth, packed FP32x2 arithmetic a further 7-9%, shared-memory loads
+    // (2 vectors + 1 broadcast per point per thread) cost in proportion
+    // to 1 / (pixels per thread).
+    const double share = (double)t.np / (t.vx * t.vy);
+    double per_pp = 1.0 - 0.65 * std::min(share, 0.25) + 0.3 * std::max(0.0, share - 0.25);
+    // packed: degree-6 0.93, degree-5 (one FMA less) 0.91, interleaved
+    // 0.89; an extra polynomial pair on every fourth point (a share of
+    // 9/32) 1.2% less again, on every second point (5/16) no change
+    static const double pk_factor[6] = {1.0, 0.93, 0.91, 0.89, 0.89, 0.879};
+    if (t.pk > 0 && t.pk < 6) per_pp *= pk_factor[t.pk];
+    per_pp += 0.5 / (t.vx * t.vy) + 0.25 / (t.pt / t.g);
+    if (t.pk == 6) per_pp = 0.69;  // measured: 0.88 of the packed degree-5 tile
+    if (t.pk >= 7) {
+        // the two-axis rotation forms run on the FMA pipe: per update
+        // 2 + 3 / VX FP32 operations (8 per MUFU cosine unit), at the
+        // measured 0.58 of the pipe's rate
+        const double f = 2.0 + 3.0 / t.vx;
+        per_pp = f / 8.0 / 0.58;
+    }
+    return waves * t.tx * t.ty * per_pp;
+}
+
+int default_direct_tile(int N, int Nx, int Ny, int sm_count) {
     double best = 1e300;
     int best_i = 0;
     for (int i = 0; i < direct_tile_count(); ++i) {
-        DirectTile t = direct_tile_get(i);
-        // CTAs are handed to SMs as earlier ones finish, so an SM's share is
-        // about ceil(CTAs / SMs) CTAs of equal work
-        long long ctas = (long long)((Nx + t.tx - 1) / t.tx) * ((Ny + t.ty - 1) / t.ty);
-        const double waves = (double)((ctas + sm_count - 1) / sm_count);
-        // Per-update cost model (in MUFU-cosine units), from the measured
-        // rates: a quarter of the cosines on the FMA pipe saves about a
-        // sixth, packed FP32x2 arithmetic a further 7-9%, shared-memory loads
-        // (2 vectors + 1 broadcast per point per thread) cost in proportion
-        // to 1 / (pixels per thread).
-        const double share = (double)t.np / (t.vx * t.vy);
-        double per_pp = 1.0 - 0.65 * std::min(share, 0.25) + 0.3 * std::max(0.0, share - 0.25);
-        // packed: degree-6 0.93, degree-5 (one FMA less) 0.91, interleaved
-        // 0.89; an extra polynomial pair on every fourth point (a share of
-        // 9/32) 1.2% less again, on every second point (5/16) no change
-        static const double pk_factor[6] = {1.0, 0.93, 0.91, 0.89, 0.89, 0.879};
-        if (t.pk > 0 && t.pk < 6) per_pp *= pk_factor[t.pk];
-        per_pp += 0.5 / (t.vx * t.vy) + 0.25 / (t.pt / t.g);
-        const double cost = waves * t.tx * t.ty * per_pp;
+        const double cost = direct_tile_cost(i, N, Nx, Ny, sm_count);
         if (cost < best - 1e-9) {
             best = cost;
             best_i = i;

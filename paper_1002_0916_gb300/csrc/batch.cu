@@ -34,7 +34,7 @@ namespace cgh {
 struct BatchPrep {  // per problem: inputs and where its tables go
     const float *points, *A, *z;
     double lambda, p;
-    int N, Npad, Nx, Ny, nxt, nyt, TX, TY;
+    int N, Npad, Nx, Ny, nxt, nyt, TX, TY, XG, YG;  // XG, YG: rotation groups (0: none)
     PointRec *rec;
     float *phx, *phy, *amp;
 };
@@ -55,15 +55,17 @@ __global__ void batch_prologue_kernel(const BatchPrep *__restrict__ prep,
 
 __global__ void batch_tables_kernel(const BatchPrep *__restrict__ prep) {
     const BatchPrep &b = prep[blockIdx.y];
-    const long long total = direct_table_entries(b.Npad, b.TX, b.TY, b.nxt, b.nyt);
+    const long long total =
+        direct_table_entries(b.Npad, b.TX, b.TY, b.nxt, b.nyt, b.XG, b.YG);
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x)
-        direct_table_entry(b.rec, b.Npad, b.TX, b.TY, b.nxt, b.nyt, e, b.phx,
+        direct_table_entry(b.rec, b.Npad, b.TX, b.TY, b.nxt, b.nyt, b.XG, b.YG, e, b.phx,
                            b.phy, b.amp);
 }
 
 template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G, int PK>
-__global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST, G>::THREADS)
+__global__ void __launch_bounds__(DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>::S::THREADS,
+                                    DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>::MIN_CTAS)
 direct_batch_kernel(const BatchTile *__restrict__ probs,
                     const uint2 *__restrict__ items, int nitems,
                     unsigned *counter, unsigned *status) {
@@ -90,8 +92,10 @@ direct_batch_kernel(const BatchTile *__restrict__ probs,
         const int ntile = bt.Npad / PT;
         typename L::Acc acc;
         acc.zero();
-        if (!L::accumulate(smem, full, &abort_flag, bt.phx + (size_t)xt * bt.Npad * TX,
-                           bt.phy + (size_t)yt * bt.Npad * TY, bt.amp, ntile, g, acc,
+        if (!L::accumulate(smem, full, &abort_flag,
+                           bt.phx + (size_t)xt * bt.Npad * TX * L::XF,
+                           bt.phy + (size_t)yt * bt.Npad * TY * L::YF, bt.amp, ntile, g,
+                           acc,
                            status))
             return;
         g += (unsigned)ntile;
@@ -105,7 +109,7 @@ static cudaError_t launch_batch_t(const BatchTile *probs, const uint2 *items,
                                   int sm_count, cudaStream_t s) {
     // probs == nullptr: only set the kernel's attributes and cache its
     // occupancy (done before any capture)
-    using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
+    using S = typename DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>::S;
     auto kern = direct_batch_kernel<TX, TY, VX, VY, PT, NST, NP, G, PK>;
     // attribute and occupancy once per device (no such calls inside a capture
     // of a geometry that has run before)
@@ -291,10 +295,12 @@ cgh_status cgh_ctx::batch_direct(const cgh_problem *probs, int count,
         b.nxt = (pr.Nx + t.tx - 1) / t.tx;
         b.nyt = (pr.Ny + t.ty - 1) / t.ty;
         b.TX = t.tx;
+        b.XG = direct_xg(t);
+        b.YG = direct_yg(t);
         b.TY = t.ty;
         b.rec = (PointRec *)(wb + off_rec[k]);
         b.phx = (float *)(wb + off_tab[k]);
-        b.phy = b.phx + (size_t)b.nxt * b.Npad * t.tx;
+        b.phy = b.phx + direct_x_floats(t, b.nxt, b.Npad);
         b.amp = (float *)(wb + off_amp[k]);
         prep.push_back(b);
         BatchTile bt;
@@ -346,8 +352,8 @@ cgh_status cgh_ctx::batch_direct(const cgh_problem *probs, int count,
     for (auto &bp : prep) maxNpad = std::max(maxNpad, bp.Npad);
     int max_entries_blocks = 1;
     for (auto &bp : prep) {
-        long long n = (long long)bp.nxt * bp.Npad * bp.TX +
-                      (long long)bp.nyt * bp.Npad * bp.TY + bp.Npad;
+        long long n = (long long)bp.nxt * bp.Npad * bp.TX * (bp.XG ? 2 : 1) +
+                      (long long)bp.nyt * bp.Npad * bp.TY * (bp.YG ? 2 : 1) + bp.Npad;
         max_entries_blocks = (int)std::max<long long>(max_entries_blocks, (n + 255) / 256);
     }
     const int np = (int)prep.size();

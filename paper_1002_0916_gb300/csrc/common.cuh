@@ -142,10 +142,13 @@ __device__ __forceinline__ void pdl_trigger() {
 namespace cgh {
 
 // Launch `kern` on stream s as a programmatic dependent of the kernel
-// before it in the stream (see pdl_wait).
+// before it in the stream (see pdl_wait), or, with dependent = false, as an
+// ordinary launch that starts only after everything before it in the stream
+// has finished.  The first kernel of every call is launched the ordinary
+// way: calls never overlap one another, whatever ran before them.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block,
-                             size_t smem, cudaStream_t s, Args &&...args) {
+cudaError_t launch_kernel(bool dependent, void (*kern)(KArgs...), dim3 grid, dim3 block,
+                          size_t smem, cudaStream_t s, Args &&...args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -155,8 +158,14 @@ cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block,
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = dependent ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block,
+                             size_t smem, cudaStream_t s, Args &&...args) {
+    return launch_kernel(true, kern, grid, block, smem, s, std::forward<Args>(args)...);
 }
 
 }  // namespace cgh
@@ -167,6 +176,25 @@ namespace cgh {
 struct DirectTile {
     int tx, ty, vx, vy, pt, np, g, pk;
 };
+
+// x-table floats per pixel column of a direct tile with packing pk: 1 (the
+// angle), or 2 for the rotation forms (pk 6 - 8: per group of a thread's
+// columns, the first column's angle, the cosines and the sines of the
+// columns' phase offsets from it); the same for the y table and rows (pk 7,
+// 8).
+__host__ __device__ constexpr int direct_xf(int pk) { return pk >= 6 ? 2 : 1; }
+__host__ __device__ constexpr int direct_yf(int pk) { return pk >= 7 ? 2 : 1; }
+// Rotation group sizes of a tile's x and y tables (0: one angle per
+// coordinate).
+inline int direct_xg(const DirectTile &t) { return direct_xf(t.pk) == 2 ? t.vx : 0; }
+inline int direct_yg(const DirectTile &t) { return direct_yf(t.pk) == 2 ? t.vy : 0; }
+// Floats of a tile's x table and y table for Npad points.
+inline size_t direct_x_floats(const DirectTile &t, int nxt, int Npad) {
+    return (size_t)nxt * Npad * t.tx * direct_xf(t.pk);
+}
+inline size_t direct_y_floats(const DirectTile &t, int nyt, int Npad) {
+    return (size_t)nyt * Npad * t.ty * direct_yf(t.pk);
+}
 
 // Number of points after padding to a multiple of `pt`.
 inline int pad_to(int n, int m) { return (n + m - 1) / m * m; }

@@ -42,10 +42,48 @@ namespace cgh {
 // operations each, which costs less than a separate kernel in the chain.
 constexpr int DT_POINTS = 16;
 
+// One coordinate w (column or row, axis 0 = x, 1 = y) of a tile's angle
+// table for the npts points of srec: dst[q * stride] = its angle for point q.
+__device__ __forceinline__ void angle_column(const PointRec *srec, int npts, int w, int axis,
+                                             float *dst, int stride) {
+    for (int q = 0; q < npts; ++q) {
+        const PointRec &r = srec[q];
+        const uint64_t b = axis ? r.by : r.bx, a = axis ? r.ay : r.ax;
+        dst[(size_t)q * stride] = (float)phase_hi(axis_phase(r.c, b, a, w)) * RAD_PER_U32;
+    }
+}
+
+// The same for a rotation table (groups of gs coordinates, T per tile; w is
+// the coordinate, i its place in the tile, row the tile's first point row):
+// coordinate k = i mod gs of its group fills slots k and gs + k of its
+// group (k = 0: the angle and 0; else the cosine and the sine of its
+// offset), with one phase difference and one sincospi per point.
+__device__ __forceinline__ void rotation_column(const PointRec *srec, int npts, int w, int i,
+                                                int T, int gs, int axis, float *row) {
+    const int ng = T / gs, g = i / gs, k = i - g * gs;
+    const int pa = rotation_pos(g, k, ng), pb = rotation_pos(g, gs + k, ng);
+    for (int q = 0; q < npts; ++q) {
+        const PointRec &r = srec[q];
+        const uint64_t b = axis ? r.by : r.bx, a = axis ? r.ay : r.ax;
+        const uint64_t p0 = axis_phase(r.c, b, a, w - k);
+        float va, vb;
+        if (k == 0) {
+            va = (float)phase_hi(p0) * RAD_PER_U32;
+            vb = 0.0f;
+        } else {
+            const uint64_t d = axis_phase(r.c, b, a, w) - p0;
+            sincospif(2.0f * ((float)phase_hi(d) * TURN_PER_U32), &vb, &va);
+        }
+        float *dst = row + (size_t)q * T * 2;
+        dst[pa] = va;
+        dst[pb] = vb;
+    }
+}
+
 template <bool FUSE>
 __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
-                                     PointSource src, int Npad, int TX, int TY,
-                                     int nxt, int nyt, float *__restrict__ phx,
+                                     PointSource src, int Npad, int TX, int TY, int XG,
+                                     int YG, int nxt, int nyt, float *__restrict__ phx,
                                      float *__restrict__ phy,
                                      float *__restrict__ amp,
                                      unsigned *__restrict__ zero, int nzero) {
@@ -73,21 +111,19 @@ __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
     const int npts = Npad - j0 < DT_POINTS ? Npad - j0 : DT_POINTS;
     if (u < nx) {
         const int t = u / TX, i = u - t * TX;
-        float *dst = phx + ((size_t)t * Npad + j0) * TX + i;
-        for (int q = 0; q < npts; ++q) {
-            const PointRec &r = srec[q];
-            dst[(size_t)q * TX] =
-                (float)phase_hi(axis_phase(r.c, r.bx, r.ax, u)) * RAD_PER_U32;
-        }
+        if (XG)
+            rotation_column(srec, npts, u, i, TX, XG, 0,
+                            phx + ((size_t)t * Npad + j0) * TX * 2);
+        else
+            angle_column(srec, npts, u, 0, phx + ((size_t)t * Npad + j0) * TX + i, TX);
     } else if (u < nx + ny) {
         const int v = u - nx;
         const int t = v / TY, i = v - t * TY;
-        float *dst = phy + ((size_t)t * Npad + j0) * TY + i;
-        for (int q = 0; q < npts; ++q) {
-            const PointRec &r = srec[q];
-            dst[(size_t)q * TY] =
-                (float)phase_hi(axis_phase(r.c, r.by, r.ay, v)) * RAD_PER_U32;
-        }
+        if (YG)
+            rotation_column(srec, npts, v, i, TY, YG, 1,
+                            phy + ((size_t)t * Npad + j0) * TY * 2);
+        else
+            angle_column(srec, npts, v, 1, phy + ((size_t)t * Npad + j0) * TY + i, TY);
     }
     if (blockIdx.y == 0 && threadIdx.x < npts) amp[j0 + threadIdx.x] = srec[threadIdx.x].A;
 }
@@ -103,14 +139,15 @@ __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
 // last, so the result is deterministic -- and writes the tile.  No CTA waits
 // for another.
 template <int TX, int TY, int VX, int VY, int PT, int NST, int NP, int G, int PK>
-__global__ void __launch_bounds__(DirectShape<TX, TY, VX, VY, PT, NST, G>::THREADS)
+__global__ void __launch_bounds__(DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>::S::THREADS,
+                                    DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>::MIN_CTAS)
 direct_fwd_kernel(const float *__restrict__ phx, const float *__restrict__ phy,
                   const float *__restrict__ amp, int Npad, int Nx, int Ny,
                   int nxt, int tail, int m, float *__restrict__ out,
                   int vec_store, float *__restrict__ part,
                   unsigned *__restrict__ count, unsigned *status) {
     using L = DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>;
-    using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
+    using S = typename L::S;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t full[NST];
     __shared__ volatile int abort_flag;
@@ -137,8 +174,8 @@ direct_fwd_kernel(const float *__restrict__ phx, const float *__restrict__ phy,
     typename L::Acc acc;
     acc.zero();
     if (!L::accumulate(smem, full, &abort_flag,
-                       phx + (size_t)xt * Npad * TX + (size_t)s0 * S::SX,
-                       phy + (size_t)yt * Npad * TY + (size_t)s0 * S::SY,
+                       phx + (size_t)xt * Npad * TX * L::XF + (size_t)s0 * S::SX,
+                       phy + (size_t)yt * Npad * TY * L::YF + (size_t)s0 * S::SY,
                        amp + (size_t)s0 * PT, s1 - s0, 0u, acc, status))
         return;
     // only the stores are left: the next kernel of the stream may launch
@@ -217,8 +254,8 @@ int direct_tile_index(const DirectTile &t) {
 
 size_t direct_phase_table_floats(const DirectTile &t, int Npad, int Nx,
                                  int Ny) {
-    size_t nxt = (Nx + t.tx - 1) / t.tx, nyt = (Ny + t.ty - 1) / t.ty;
-    return nxt * Npad * t.tx + nyt * Npad * t.ty;
+    const int nxt = (Nx + t.tx - 1) / t.tx, nyt = (Ny + t.ty - 1) / t.ty;
+    return direct_x_floats(t, nxt, Npad) + direct_y_floats(t, nyt, Npad);
 }
 
 static cudaError_t launch_tables(const PointRec *rec, const PointSource *src,
@@ -228,13 +265,14 @@ static cudaError_t launch_tables(const PointRec *rec, const PointSource *src,
     int nxt = (Nx + t.tx - 1) / t.tx, nyt = (Ny + t.ty - 1) / t.ty;
     const int span = nxt * t.tx + nyt * t.ty;  // <= 65536 + 2 tiles
     dim3 grid((Npad + DT_POINTS - 1) / DT_POINTS, (span + 255) / 256);
-    if (src)
-        return launch_dependent(direct_tables_kernel<true>, grid, dim3(256), 0, s,
-                                (const PointRec *)nullptr, *src, Npad, t.tx, t.ty,
-                                nxt, nyt, phx, phy, amp, zero, nzero);
+    const int xg = direct_xg(t), yg = direct_yg(t);
+    if (src)  // (builds the records itself: the call's first kernel)
+        return launch_kernel(false, direct_tables_kernel<true>, grid, dim3(256), 0, s,
+                             (const PointRec *)nullptr, *src, Npad, t.tx, t.ty, xg, yg, nxt,
+                             nyt, phx, phy, amp, zero, nzero);
     return launch_dependent(direct_tables_kernel<false>, grid, dim3(256), 0, s, rec,
-                            PointSource{}, Npad, t.tx, t.ty, nxt, nyt, phx, phy, amp,
-                            zero, nzero);
+                            PointSource{}, Npad, t.tx, t.ty, xg, yg, nxt, nyt, phx, phy,
+                            amp, zero, nzero);
 }
 
 cudaError_t launch_direct_tables(const PointRec *rec, int Npad, int Nx, int Ny,
@@ -277,7 +315,7 @@ static cudaError_t launch_one(const float *phx, const float *phy,
                               const float *amp, int Npad, int Nx, int Ny,
                               float *out, const DirectSplit &d, float *part,
                               unsigned *count, unsigned *status, cudaStream_t s) {
-    using S = DirectShape<TX, TY, VX, VY, PT, NST, G>;
+    using S = typename DirectTileLoop<TX, TY, VX, VY, PT, NST, NP, G, PK>::S;
     auto kern = direct_fwd_kernel<TX, TY, VX, VY, PT, NST, NP, G, PK>;
     static bool attr_set[64] = {};
     int dev = 0;

@@ -139,6 +139,30 @@ ScratchPlan plan_scratch(const DirectTile &t, int Npad, int Nx, int Ny,
     return s;
 }
 
+// The tile for N > 0 points: the heuristic's, or its cheapest whose scratch
+// without the split tail fits the array; -1 if none fits.
+int noalloc_tile(int N, int Nx, int Ny, int sms) {
+    const auto fits = [&](int i) {
+        const DirectTile t = direct_tile_get(i);
+        const int Npad = pad_to(N, t.pt);
+        const DirectSplit d = direct_split_plan(i, sms, Npad, Nx, Ny, false);
+        return plan_scratch(t, Npad, Nx, Ny, d).total <= (size_t)CGH_NOALLOC_SCRATCH_BYTES;
+    };
+    const int first = default_direct_tile(N, Nx, Ny, sms);
+    if (fits(first)) return first;
+    int best = -1;
+    double best_cost = 0.0;
+    for (int i = 0; i < direct_tile_count(); ++i) {
+        if (!fits(i)) continue;
+        const double c = direct_tile_cost(i, N, Nx, Ny, sms);
+        if (best < 0 || c < best_cost - 1e-9) {
+            best = i;
+            best_cost = c;
+        }
+    }
+    return best;
+}
+
 }  // namespace
 
 extern "C" cgh_status cgh_forward_noalloc(const float *points, const float *A,
@@ -167,9 +191,12 @@ extern "C" cgh_status cgh_forward_noalloc(const float *points, const float *A,
         return CGH_ERR_CUDA;
     }
 
-    // the heuristic's tile with the split tail, else without it, if the
-    // scratch fits the array (N = 0 needs none)
-    const int tile_index = default_direct_tile(N, Nx, Ny, sms);
+    // the heuristic's tile if its tables fit the array, else the
+    // heuristic's best among the tiles whose tables fit; with the split
+    // tail, else without it, if that scratch fits too (N = 0 needs none)
+    const int tile_index =
+        N > 0 ? noalloc_tile(N, Nx, Ny, sms) : default_direct_tile(N, Nx, Ny, sms);
+    if (tile_index < 0) return CGH_ERR_UNSUPPORTED;  // no tile's tables fit the array
     const DirectTile t = direct_tile_get(tile_index);
     const int Npad = pad_to(N > 0 ? N : 1, t.pt);
     DirectSplit d = direct_split_plan(tile_index, sms, Npad, Nx, Ny, true);
@@ -191,7 +218,7 @@ extern "C" cgh_status cgh_forward_noalloc(const float *points, const float *A,
     unsigned *status = (unsigned *)b;
     const int nxt = (Nx + t.tx - 1) / t.tx;
     float *phx = (float *)(b + sp.tab_off);
-    float *phy = phx + (size_t)nxt * Npad * t.tx;
+    float *phy = phx + direct_x_floats(t, nxt, Npad);
     float *amp = (float *)(b + sp.amp_off);
     const int nsplit = d.tiles - d.tail;
     float *part = nsplit ? (float *)(b + sp.part_off) : nullptr;

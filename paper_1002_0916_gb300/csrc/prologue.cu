@@ -37,8 +37,9 @@ cudaError_t launch_prologue(const float *points, const float *A,
     // the points thinly over many SMs
     int threads = 32;
     int blocks = (Npad + threads - 1) / threads;
-    return launch_dependent(prologue_kernel, dim3(blocks), dim3(threads), 0, s, points,
-                            A, z, N, Npad, lambda, p, rec, status, y0);
+    // (the first kernel of its call: an ordinary launch)
+    return launch_kernel(false, prologue_kernel, dim3(blocks), dim3(threads), 0, s, points,
+                         A, z, N, Npad, lambda, p, rec, status, y0);
 }
 
 }  // namespace cgh

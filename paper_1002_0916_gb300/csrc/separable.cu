@@ -75,14 +75,15 @@ cudaError_t launch_sep_tables(const PointSource &src, int Npad, int Nx, int Ny, 
                               cudaStream_t s) {
     const int rows = Nx + Ny;  // <= 65536: grid y stays below its limit
     dim3 grid((Npad + ST_POINTS - 1) / ST_POINTS, (rows + ST_BLOCK_ROWS - 1) / ST_BLOCK_ROWS);
+    // (builds the records itself: the call's first kernel, an ordinary launch)
     if (kind == 0)
-        return launch_dependent(sep_tables_kernel<0>, grid, dim3(256), 0, s, src, Npad, Nx,
-                                Ny, Kp, Lhi, Llo, Rhi, Rlo);
+        return launch_kernel(false, sep_tables_kernel<0>, grid, dim3(256), 0, s, src, Npad,
+                             Nx, Ny, Kp, Lhi, Llo, Rhi, Rlo);
     if (kind == 1)
-        return launch_dependent(sep_tables_kernel<1>, grid, dim3(256), 0, s, src, Npad, Nx,
-                                Ny, Kp, Lhi, Llo, Rhi, Rlo);
-    return launch_dependent(sep_tables_kernel<2>, grid, dim3(256), 0, s, src, Npad, Nx, Ny,
-                            Kp, Lhi, Llo, Rhi, Rlo);
+        return launch_kernel(false, sep_tables_kernel<1>, grid, dim3(256), 0, s, src, Npad,
+                             Nx, Ny, Kp, Lhi, Llo, Rhi, Rlo);
+    return launch_kernel(false, sep_tables_kernel<2>, grid, dim3(256), 0, s, src, Npad, Nx,
+                         Ny, Kp, Lhi, Llo, Rhi, Rlo);
 }
 
 }  // namespace cgh

@@ -27,8 +27,10 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map,
 }
 
 // ----------------------------------------------------------------- TMEM
-// Allocation and release are executed by one whole warp.
+// Allocation and release are executed by one whole warp, joined first (the
+// instructions are .sync.aligned).
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+    __syncwarp();
     asm volatile(
         "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
             smem_u32(dst_smem)),
@@ -37,11 +39,13 @@ __device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
 }
 
 __device__ __forceinline__ void tmem_relinquish() {
+    __syncwarp();
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::
                      : "memory");
 }
 
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
                  "r"(ncols)
                  : "memory");

@@ -25,8 +25,11 @@ __device__ __forceinline__ uint32_t map_to_rank(const void *p, uint32_t rank) {
     return out;
 }
 
-// Every thread of both CTAs.
+// Every thread of both CTAs.  The .aligned barrier wants each warp
+// converged: role branches (one lane producing, one issuing MMAs) may leave
+// a warp split, so it is joined first.
 __device__ __forceinline__ void cluster_sync() {
+    __syncwarp();
     asm volatile(
         "barrier.cluster.arrive.release.aligned;\n"
         "barrier.cluster.wait.acquire.aligned;" ::
@@ -55,8 +58,10 @@ __device__ __forceinline__ bool wait_cluster_bounded(uint64_t *bar, uint32_t par
     return true;
 }
 
-// Tensor memory of a CTA pair: one warp of each CTA, collectively.
+// Tensor memory of a CTA pair: one warp of each CTA, collectively (each
+// helper joins the warp first: the instructions are .sync.aligned).
 __device__ __forceinline__ void tmem_alloc2(uint32_t *dst_smem, uint32_t ncols) {
+    __syncwarp();
     asm volatile(
         "tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
             smem_u32(dst_smem)),
@@ -65,11 +70,13 @@ __device__ __forceinline__ void tmem_alloc2(uint32_t *dst_smem, uint32_t ncols) 
 }
 
 __device__ __forceinline__ void tmem_relinquish2() {
+    __syncwarp();
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::
                      : "memory");
 }
 
 __device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols) {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr),
                  "r"(ncols)
                  : "memory");

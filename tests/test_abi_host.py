@@ -53,9 +53,13 @@ def test_tile_registry(cg):
     for tx, ty, vx, vy, pt, np_, g, pk in tiles:
         assert tx % vx == 0 and ty % vy == 0 and pt % (4 * g) == 0
         assert g * (tx // vx) * (ty // vy) == 256 and 0 <= np_ <= vx * vy
-        assert pk in (0, 1, 2, 3, 4, 5) and (pk == 0 or (vx % 2 == 0 and np_ % 2 == 0))
-        if pk >= 4:   # one extra polynomial pair on every second or fourth point
+        assert pk in range(9) and (pk == 0 or (vx % 2 == 0 and np_ % 2 == 0))
+        if pk in (4, 5):   # one extra polynomial pair on every second or fourth point
             assert np_ + 2 <= vx * vy and (pt // g) % (2 if pk == 4 else 4) == 0
+        if pk == 6:        # the row rotation form: rows of 4 pixels, no polynomial
+            assert vx == 4 and np_ == 0 and (pt // g) % 4 == 0
+        if pk in (7, 8):   # the two-axis rotation form: groups in fours along both axes
+            assert vy % 2 == 0 and np_ == 0 and (pt // g) % 4 == 0
 
 
 def test_null_handle_is_rejected(cg):

@@ -47,3 +47,36 @@ def test_fma_only_recipes():
     assert bench.SIMT_PP_PER_CLK_PER_SM == 128 / 2
     assert bench.BWD_SIMT_PP_PER_CLK_PER_SM == 128 / 4
     assert bench.RECUR_PP_PER_CLK_PER_SM == 16
+
+
+def _rotation_ops(vx, vy, packed):
+    """FP32 operations of one point on one thread's vx x vy block in the
+    two-axis rotation form, counted operation by operation."""
+    ops = 1 + 1 + 2                    # angle add, sincos argument scale, A cos, A sin
+    for i in range(vy):
+        if i > 0:
+            ops += 4                   # the row's (Re w, Im w) by angle addition
+        for k in range(vx):
+            if packed:
+                ops += 2               # every pixel: two lanes of two packed FMAs
+            else:
+                ops += 1 if k == 0 else 2
+    return ops
+
+
+def test_rotation_recipes():
+    for tile in [(64, 32, 16, 4, 64, 0, 8, 7), (64, 32, 8, 4, 32, 0, 4, 7),
+                 (32, 32, 4, 4, 64, 0, 4, 8), (64, 64, 16, 4, 32, 0, 4, 8)]:
+        vx, vy, pk = tile[2], tile[3], tile[7]
+        per_clk, _, measured, mufu = bench.alu_recipe("direct", tile)
+        f = _rotation_ops(vx, vy, pk == 8) / (vx * vy)
+        assert abs(per_clk - 128.0 / f) < 1e-9
+        assert abs(measured(16.0, 128.0) - per_clk) < 1e-9
+        assert abs(mufu - 2.0 / (vx * vy)) < 1e-12
+    # the row rotation form: a sincos per 4 pixels bounds it at 32
+    per_clk, _, measured, _ = bench.alu_recipe("batch", (32, 32, 4, 4, 64, 0, 4, 6))
+    assert per_clk == 32.0 and measured(16.0, 128.0) == 32.0
+    # without a tile (or with a cosine-per-pixel tile) the mixed recipe stays
+    assert bench.alu_recipe("direct")[0] == bench.MIXED_PP_PER_CLK_PER_SM
+    assert bench.alu_recipe("direct", (32, 32, 4, 4, 64, 4, 4, 5))[0] == \
+        bench.MIXED_PP_PER_CLK_PER_SM
