@@ -33,9 +33,10 @@
 namespace cgh {
 
 // ------------------------------------------------------------ tables
-// One block per DT_POINTS points (grid x) and 256 pixel columns/rows (grid
-// y) of the concatenated x and y ranges: the records are staged in shared
-// memory once, each thread then writes its coordinate for every point.
+// One block per DT_POINTS points (grid x) and 256 pixel columns or rows
+// (grid y: the x range, then the y range): the records are staged in shared
+// memory once; each thread then writes its coordinate for every point, or,
+// in a rotation table, four coordinates of a group for one point at a time.
 // FUSE: the block builds its DT_POINTS records itself from the caller's
 // points (step A1, as in prologue.cu) instead of reading them from `rec`;
 // each record is then built once per block row of grid y, a few FP64
@@ -53,31 +54,36 @@ __device__ __forceinline__ void angle_column(const PointRec *srec, int npts, int
     }
 }
 
-// The same for a rotation table (groups of gs coordinates, T per tile; w is
-// the coordinate, i its place in the tile, row the tile's first point row):
-// coordinate k = i mod gs of its group fills slots k and gs + k of its
-// group (k = 0: the angle and 0; else the cosine and the sine of its
-// offset), with one phase difference and one sincospi per point.
-__device__ __forceinline__ void rotation_column(const PointRec *srec, int npts, int w, int i,
-                                                int T, int gs, int axis, float *row) {
-    const int ng = T / gs, g = i / gs, k = i - g * gs;
-    const int pa = rotation_pos(g, k, ng), pb = rotation_pos(g, gs + k, ng);
-    for (int q = 0; q < npts; ++q) {
-        const PointRec &r = srec[q];
-        const uint64_t b = axis ? r.by : r.bx, a = axis ? r.ay : r.ax;
-        const uint64_t p0 = axis_phase(r.c, b, a, w - k);
-        float va, vb;
-        if (k == 0) {
-            va = (float)phase_hi(p0) * RAD_PER_U32;
-            vb = 0.0f;
+// Four coordinates g0 + k0 .. g0 + k0 + 3 (k0 = 4 h) of one rotation group
+// of gs coordinates along an axis (0 = x, 1 = y), for one point: slots k0 ..
+// k0 + 3 (cosines of the offsets; slot 0 is the angle at g0) and gs + k0 ..
+// gs + k0 + 3 (sines; slot gs is 0), one 16-byte store each into the
+// point's row of the table (ng groups per tile).  The offsets are exact in
+// fixed point: Phi(g0 + k) - Phi(g0) = k (c (2 g0 + k) - b) for the first,
+// then each next one adds the first difference c (2 u + 1) - b, which grows
+// by 2 c per coordinate (Eq. 2 on the axis).
+__device__ __forceinline__ void rotation_quarter(const PointRec &r, int axis, int g0, int g,
+                                                 int h, int gs, int ng, float *row) {
+    const uint64_t c = r.c, b = axis ? r.by : r.bx, a = axis ? r.ay : r.ax;
+    const int k0 = 4 * h;
+    uint64_t d = (uint64_t)k0 * (c * (uint64_t)(2 * g0 + k0) - b);
+    uint64_t step = c * (uint64_t)(2 * (g0 + k0) + 1) - b;
+    float co[4], si[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (k0 + i == 0) {
+            co[i] = (float)phase_hi(axis_phase(c, b, a, g0)) * RAD_PER_U32;
+            si[i] = 0.0f;
         } else {
-            const uint64_t d = axis_phase(r.c, b, a, w) - p0;
-            sincospif(2.0f * ((float)phase_hi(d) * TURN_PER_U32), &vb, &va);
+            sincospif(2.0f * ((float)phase_hi(d) * TURN_PER_U32), &si[i], &co[i]);
         }
-        float *dst = row + (size_t)q * T * 2;
-        dst[pa] = va;
-        dst[pb] = vb;
+        d += step;
+        step += 2 * c;
     }
+    *reinterpret_cast<float4 *>(row + rotation_pos(g, k0, ng)) =
+        make_float4(co[0], co[1], co[2], co[3]);
+    *reinterpret_cast<float4 *>(row + rotation_pos(g, gs + k0, ng)) =
+        make_float4(si[0], si[1], si[2], si[3]);
 }
 
 template <bool FUSE>
@@ -106,24 +112,28 @@ __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
             srec[threadIdx.x] = rec[j0 + threadIdx.x];
     }
     __syncthreads();
-    const int u = blockIdx.y * blockDim.x + threadIdx.x;
-    const int nx = nxt * TX, ny = nyt * TY;
+    // grid y: the x coordinates in blocks of 256, then the y coordinates
+    const int nx = nxt * TX, ny = nyt * TY, nbx = (nx + 255) / 256;
+    const int axis = (int)blockIdx.y >= nbx ? 1 : 0;
+    const int w0 = ((int)blockIdx.y - axis * nbx) * 256;  // the block's first coordinate
+    const int n = axis ? ny : nx, T = axis ? TY : TX, gs = axis ? YG : XG;
+    float *tab = axis ? phy : phx;
     const int npts = Npad - j0 < DT_POINTS ? Npad - j0 : DT_POINTS;
-    if (u < nx) {
-        const int t = u / TX, i = u - t * TX;
-        if (XG)
-            rotation_column(srec, npts, u, i, TX, XG, 0,
-                            phx + ((size_t)t * Npad + j0) * TX * 2);
-        else
-            angle_column(srec, npts, u, 0, phx + ((size_t)t * Npad + j0) * TX + i, TX);
-    } else if (u < nx + ny) {
-        const int v = u - nx;
-        const int t = v / TY, i = v - t * TY;
-        if (YG)
-            rotation_column(srec, npts, v, i, TY, YG, 1,
-                            phy + ((size_t)t * Npad + j0) * TY * 2);
-        else
-            angle_column(srec, npts, v, 1, phy + ((size_t)t * Npad + j0) * TY + i, TY);
+    if (gs) {
+        // a rotation table: one thread per four coordinates and point
+        for (int it = threadIdx.x; it < 64 * npts; it += blockDim.x) {
+            const int w = w0 + 4 * (it & 63), q = it >> 6;
+            if (w >= n) continue;
+            const int t = w / T, i = w - t * T, g = i / gs, h = (i - g * gs) >> 2;
+            rotation_quarter(srec[q], axis, w - 4 * h, g, h, gs, T / gs,
+                             tab + ((size_t)t * Npad + j0 + q) * T * 2);
+        }
+    } else {
+        const int u = w0 + threadIdx.x;
+        if (u < n) {
+            const int t = u / T, i = u - t * T;
+            angle_column(srec, npts, u, axis, tab + ((size_t)t * Npad + j0) * T + i, T);
+        }
     }
     if (blockIdx.y == 0 && threadIdx.x < npts) amp[j0 + threadIdx.x] = srec[threadIdx.x].A;
 }
@@ -263,8 +273,9 @@ static cudaError_t launch_tables(const PointRec *rec, const PointSource *src,
                                  float *phx, float *phy, float *amp,
                                  unsigned *zero, int nzero, cudaStream_t s) {
     int nxt = (Nx + t.tx - 1) / t.tx, nyt = (Ny + t.ty - 1) / t.ty;
-    const int span = nxt * t.tx + nyt * t.ty;  // <= 65536 + 2 tiles
-    dim3 grid((Npad + DT_POINTS - 1) / DT_POINTS, (span + 255) / 256);
+    // grid y: the x coordinates, then the y coordinates, in blocks of 256
+    const int nby = (nxt * t.tx + 255) / 256 + (nyt * t.ty + 255) / 256;
+    dim3 grid((Npad + DT_POINTS - 1) / DT_POINTS, nby);
     const int xg = direct_xg(t), yg = direct_yg(t);
     if (src)  // (builds the records itself: the call's first kernel)
         return launch_kernel(false, direct_tables_kernel<true>, grid, dim3(256), 0, s,

@@ -55,7 +55,6 @@ namespace cgh {
     X(32, 32, 4, 4, 64, 3, 4, 4, 4)        \
     X(32, 32, 4, 4, 64, 3, 4, 4, 5)        \
     X(32, 32, 4, 4, 64, 3, 0, 4, 6)        \
-    X(32, 32, 4, 4, 32, 3, 0, 4, 6)        \
     X(32, 32, 4, 4, 64, 3, 0, 4, 7)        \
     X(32, 32, 8, 4, 64, 3, 0, 8, 7)        \
     X(64, 32, 8, 4, 32, 3, 0, 4, 7)        \
@@ -65,9 +64,7 @@ namespace cgh {
     X(64, 32, 16, 4, 64, 2, 0, 8, 7)       \
     X(64, 32, 8, 4, 32, 3, 0, 4, 8)        \
     X(64, 64, 8, 4, 32, 3, 0, 2, 8)        \
-    X(32, 32, 4, 4, 64, 3, 0, 4, 8)        \
-    X(64, 64, 16, 4, 32, 3, 0, 4, 8)       \
-    X(64, 32, 16, 4, 64, 2, 0, 8, 8)
+    X(32, 32, 4, 4, 64, 3, 0, 4, 8)
 
 // ------------------------------------------------------------- tables
 // The rotation tables.  Along an axis with rotation group size gs (the
@@ -306,17 +303,17 @@ struct DirectTileLoop {
     static_assert(!PK || NP % 2 == 0, "packed pairs take the polynomial together");
     static_assert(PKV < 4 || PKV >= 6 || (NP / 2 + 1 <= NPAIRS && (PT / G) % PERIOD == 0),
                   "the extra polynomial pair fits and the periods tile a stage");
-    static_assert(PKV < 6 || (VX % 2 == 0 && NP == 0 && (PT / G) % 4 == 0),
-                  "the rotation forms: column groups in fours, no polynomial, points in "
-                  "fours");
+    static_assert(PKV < 6 || (VX % 4 == 0 && NP == 0 && (PT / G) % 4 == 0),
+                  "the rotation forms: columns in fours, no polynomial, points in fours");
     static_assert(PKV != 6 || VX == 4, "the row rotation form: 4 columns");
-    static_assert(PKV < 7 || VY % 2 == 0, "the two-axis rotation form: row groups in fours");
+    static_assert(PKV < 7 || VY % 4 == 0, "the two-axis rotation form: rows in fours");
     static constexpr int XF = direct_xf(PKV);
     static constexpr int YF = direct_yf(PKV);
     using S = DirectShape<TX, TY, VX, VY, PT, NST, G, XF, YF>;
-    // CTAs per SM the register allocation must leave room for: two for the
-    // rotation forms' 64-pixel blocks (at most 128 registers a thread)
-    static constexpr int MIN_CTAS = (PKV >= 7 && VX * VY >= 64) ? 2 : 1;
+    // CTAs per SM the register allocation must leave room for: for the
+    // rotation forms, two with 64-pixel blocks (at most 128 registers a
+    // thread), three with 32-pixel blocks (at most 85)
+    static constexpr int MIN_CTAS = PKV < 7 ? 1 : VX * VY >= 64 ? 2 : 3;
     // (the two-axis rotation form updates its pixels one by one)
     using Acc = DirectAcc<VY, VX, PK && PKV != 7>;
     static_assert(PKV != 8 || VX % 4 == 0, "the packed two-axis form: column groups of 4 or 8");

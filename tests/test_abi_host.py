@@ -59,7 +59,7 @@ def test_tile_registry(cg):
         if pk == 6:        # the row rotation form: rows of 4 pixels, no polynomial
             assert vx == 4 and np_ == 0 and (pt // g) % 4 == 0
         if pk in (7, 8):   # the two-axis rotation form: groups in fours along both axes
-            assert vy % 2 == 0 and np_ == 0 and (pt // g) % 4 == 0
+            assert vx % 4 == 0 and vy % 4 == 0 and np_ == 0 and (pt // g) % 4 == 0
 
 
 def test_null_handle_is_rejected(cg):
