@@ -155,7 +155,7 @@ cgh_status cgh_ctx::forward_direct(const float *points, const float *A,
         cudaError_t e =
             direct_fused_tables
                 ? launch_direct_tables_fused(
-                      PointSource{points, A, z, N, lambda, p, d_status, row_origin}, Npad, Nx, Ny,
+                      PointSource{points, A, z, N, fresnel_scale(lambda, p), d_status, row_origin}, Npad, Nx, Ny,
                       t, phx, phy, amp, count, nsplit, s)
                 : launch_direct_tables(rec, Npad, Nx, Ny, t, phx, phy, amp, count,
                                        nsplit, s);

@@ -33,7 +33,7 @@ namespace cgh {
 
 struct BatchPrep {  // per problem: inputs and where its tables go
     const float *points, *A, *z;
-    double lambda, p;
+    double K;  // fresnel_scale(lambda, p)
     int N, Npad, Nx, Ny, nxt, nyt, TX, TY, XG, YG;  // XG, YG: rotation groups (0: none)
     PointRec *rec;
     float *phx, *phy, *amp;
@@ -50,7 +50,7 @@ __global__ void batch_prologue_kernel(const BatchPrep *__restrict__ prep,
     const BatchPrep &b = prep[blockIdx.y];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < b.Npad;
          j += gridDim.x * blockDim.x)
-        b.rec[j] = make_point_rec(b.points, b.A, b.z, b.N, j, b.lambda, b.p, status);
+        b.rec[j] = make_point_rec(b.points, b.A, b.z, b.N, j, b.K, status);
 }
 
 __global__ void batch_tables_kernel(const BatchPrep *__restrict__ prep) {
@@ -286,8 +286,7 @@ cgh_status cgh_ctx::batch_direct(const cgh_problem *probs, int count,
         b.points = pr.points;
         b.A = pr.A;
         b.z = pr.z;
-        b.lambda = pr.lambda;
-        b.p = pr.p;
+        b.K = fresnel_scale(pr.lambda, pr.p);
         b.N = pr.N;
         b.Npad = pad_to(pr.N, t.pt);
         b.Nx = pr.Nx;
@@ -539,7 +538,7 @@ extern "C" cgh_status cgh_tune_batch(cgh_handle h, const cgh_problem *probs,
 
 struct SepPrep {  // per problem: inputs and where its U/V tables go
     const float *points, *A, *z;
-    double lambda, p;
+    double K;  // fresnel_scale(lambda, p)
     int N, Npad, Nx, Ny, Kp;
     PointRec *rec;
     void *Lhi, *Llo, *Rhi, *Rlo;
@@ -550,7 +549,7 @@ __global__ void sep_batch_prologue_kernel(const SepPrep *__restrict__ prep,
     const SepPrep &b = prep[blockIdx.y];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < b.Npad;
          j += gridDim.x * blockDim.x)
-        b.rec[j] = make_point_rec(b.points, b.A, b.z, b.N, j, b.lambda, b.p, status);
+        b.rec[j] = make_point_rec(b.points, b.A, b.z, b.N, j, b.K, status);
 }
 
 // Work items of one problem: (point pair, group of ST_ROWS table rows),
@@ -609,8 +608,7 @@ cgh_status cgh_ctx::batch_separable(const cgh_problem *probs, int count,
         sp.points = pr.points;
         sp.A = pr.A;
         sp.z = pr.z;
-        sp.lambda = pr.lambda;
-        sp.p = pr.p;
+        sp.K = fresnel_scale(pr.lambda, pr.p);
         sp.N = pr.N;
         sp.Npad = Kp / 2;
         sp.Nx = pr.Nx;

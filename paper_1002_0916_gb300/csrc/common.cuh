@@ -217,10 +217,14 @@ cudaError_t launch_direct_tables(const PointRec *rec, int Npad, int Nx, int Ny,
                                  float *amp, unsigned *zero, int nzero,
                                  cudaStream_t s);
 // The caller's point arrays, for kernels that build the records themselves.
+// p^2 / (2 lambda): Q_j = P_j / (2 pi) = this / z_j turns per pixel^2 (the
+// definition of P_j under Eq. 1), the part of Q_j shared by every point.
+inline double fresnel_scale(double lambda, double p) { return p * p / (2.0 * lambda); }
+
 struct PointSource {
     const float *points, *A, *z;
     int N;
-    double lambda, p;
+    double K;  // fresnel_scale(lambda, p)
     unsigned *status;
     int y0 = 0;  // origin of the pixel rows (see make_point_rec)
 };

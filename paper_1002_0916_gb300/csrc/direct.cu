@@ -107,7 +107,7 @@ __global__ void direct_tables_kernel(const PointRec *__restrict__ rec,
         if constexpr (FUSE)
             srec[threadIdx.x] =
                 make_point_rec(src.points, src.A, src.z, src.N, j0 + threadIdx.x,
-                               src.lambda, src.p, src.status, src.y0);
+                               src.K, src.status, src.y0);
         else
             srec[threadIdx.x] = rec[j0 + threadIdx.x];
     }

@@ -229,7 +229,7 @@ extern "C" cgh_status cgh_forward_noalloc(const float *points, const float *A,
         e = cudaMemsetAsync(out, 0, (size_t)Nx * Ny * sizeof(float), s);
     if (e == cudaSuccess && N > 0) {
         // (the tables kernel also zeroes the split schedule's counters)
-        e = launch_direct_tables_fused(PointSource{points, A, z, N, lambda, p, status},
+        e = launch_direct_tables_fused(PointSource{points, A, z, N, fresnel_scale(lambda, p), status},
                                        Npad, Nx, Ny, t, phx, phy, amp, count, nsplit, s);
         if (e == cudaSuccess)
             e = launch_direct_forward(tile_index, phx, phy, amp, Npad, Nx, Ny, out, d,

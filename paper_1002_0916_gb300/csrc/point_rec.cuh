@@ -8,15 +8,18 @@
 
 namespace cgh {
 
-// f in [0, 1) -> round-down 0.64 fixed point (error < 2^-64 turns).
+// f in [0, 1) -> round-down 0.64 fixed point, floor(f 2^64) exactly, from
+// the bits of f (integer operations only: FP64 is slow on this GPU):
+// f = m 2^(e - 1075) with the 53-bit significand m and biased exponent e.
 __device__ __forceinline__ uint64_t to_fix64(double f) {
-    double u = f * 4294967296.0;          // exact scaling
-    double hi = floor(u);                 // < 2^32
-    double lo = floor((u - hi) * 4294967296.0);
-    return ((uint64_t)hi << 32) | (uint64_t)lo;
+    const uint64_t bits = (uint64_t)__double_as_longlong(f);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    if (e == 0) return 0;  // zero or subnormal: below 2^-1022
+    const uint64_t m = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = e - 1011;  // f 2^64 = m 2^sh; f < 1 gives sh <= 11
+    if (sh >= 0) return m << sh;
+    return sh > -64 ? m >> -sh : 0;
 }
-
-__device__ __forceinline__ double frac(double v) { return v - floor(v); }
 
 // |x| = m 2^-s exactly, with m a 24-bit integer (frexpf) and s an integer
 // shift (negative for |x| >= 2^24).
@@ -58,8 +61,8 @@ __device__ __forceinline__ uint64_t mul_shift(uint64_t c, uint64_t v, int s) {
 __device__ __forceinline__ PointRec make_point_rec(const float *points,
                                                    const float *A,
                                                    const float *z, int N, int j,
-                                                   double lambda, double p,
-                                                   unsigned *status, int y0 = 0) {
+                                                   double K, unsigned *status,
+                                                   int y0 = 0) {
     PointRec r;
     r.c = r.bx = r.ax = r.by = r.ay = 0;
     r.A = 0.0f;
@@ -67,7 +70,14 @@ __device__ __forceinline__ PointRec make_point_rec(const float *points,
     if (j < N) {
         const float xj = points[2 * j], yj = points[2 * j + 1];
         const float aj = A[j], zj = z[j];
-        const double Q = (p * p) / (2.0 * lambda * (double)zj);
+        // Q_j = K / z_j with K = p^2 / (2 lambda) from the host: 1 / z_j from
+        // the FP32 reciprocal and two Newton steps in FP64 (relative error
+        // 2^-23 -> 2^-46 -> FP64 rounding), no FP64 division
+        const double zd = (double)zj;
+        double rz = (double)__frcp_rn(zj);
+        rz = fma(fma(-zd, rz, 1.0), rz, rz);
+        rz = fma(fma(-zd, rz, 1.0), rz, rz);
+        const double Q = K * rz;
         const bool ok = isfinite(xj) && isfinite(yj) && isfinite(aj) &&
                         isfinite(zj) && zj > 0.0f && Q < 1.0;
         if (ok) {

@@ -18,14 +18,13 @@ namespace cgh {
 __global__ void prologue_kernel(const float *__restrict__ points,
                                 const float *__restrict__ A,
                                 const float *__restrict__ z, int N, int Npad,
-                                double lambda, double p,
-                                PointRec *__restrict__ rec,
+                                double K, PointRec *__restrict__ rec,
                                 unsigned *status, int y0) {
     pdl_wait();  // the inputs may come from the kernel before
     pdl_trigger();
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= Npad) return;
-    rec[j] = make_point_rec(points, A, z, N, j, lambda, p, status, y0);
+    rec[j] = make_point_rec(points, A, z, N, j, K, status, y0);
 }
 
 cudaError_t launch_prologue(const float *points, const float *A,
@@ -39,7 +38,7 @@ cudaError_t launch_prologue(const float *points, const float *A,
     int blocks = (Npad + threads - 1) / threads;
     // (the first kernel of its call: an ordinary launch)
     return launch_kernel(false, prologue_kernel, dim3(blocks), dim3(threads), 0, s, points,
-                         A, z, N, Npad, lambda, p, rec, status, y0);
+                         A, z, N, Npad, fresnel_scale(lambda, p), rec, status, y0);
 }
 
 }  // namespace cgh

@@ -55,7 +55,7 @@ sep_tables_kernel(PointSource src, int Npad, int Nx, int Ny, int Kp,
     const int j0 = blockIdx.x * ST_POINTS;
     if (threadIdx.x < ST_POINTS && j0 + (int)threadIdx.x < Npad)
         srec[threadIdx.x] = make_point_rec(src.points, src.A, src.z, src.N,
-                                           j0 + threadIdx.x, src.lambda, src.p,
+                                           j0 + threadIdx.x, src.K,
                                            src.status, src.y0);
     __syncthreads();
     const int pair = threadIdx.x & 31, run = threadIdx.x >> 5;
@@ -153,7 +153,7 @@ cgh_status cgh_ctx::forward_separable(const float *points, const float *A,
         // the tables kernel builds the point records itself (no prologue)
         TimedLaunch tl(this, CGH_K_SEP_TABLES, s);
         cudaError_t e = launch_sep_tables(
-            PointSource{points, A, z, N, lambda, p, d_status, row_origin}, Npad, Nx, Ny,
+            PointSource{points, A, z, N, fresnel_scale(lambda, p), d_status, row_origin}, Npad, Nx, Ny,
             Kp, kind, Lhi, Llo, Rhi, Rlo, s);
         if (e != cudaSuccess) return cuda_fail(e, "separable tables launch");
         tl.done();
