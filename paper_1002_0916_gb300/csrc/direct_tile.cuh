@@ -62,9 +62,12 @@ namespace cgh {
     X(64, 32, 8, 4, 64, 2, 0, 4, 7)        \
     X(64, 64, 16, 4, 32, 3, 0, 4, 7)       \
     X(64, 32, 16, 4, 64, 2, 0, 8, 7)       \
+    X(64, 64, 8, 8, 32, 3, 0, 4, 7)        \
+    X(64, 32, 8, 8, 64, 2, 0, 8, 7)        \
     X(64, 32, 8, 4, 32, 3, 0, 4, 8)        \
     X(64, 64, 8, 4, 32, 3, 0, 2, 8)        \
-    X(32, 32, 4, 4, 64, 3, 0, 4, 8)
+    X(32, 32, 4, 4, 64, 3, 0, 4, 8)        \
+    X(64, 64, 8, 8, 32, 3, 0, 4, 8)
 
 // ------------------------------------------------------------- tables
 // The rotation tables.  Along an axis with rotation group size gs (the
