@@ -48,34 +48,46 @@ def _small_clouds():
             for i, (Nx, Ny, N) in enumerate(shapes)]
 
 
+def _batch_tiles(cg):
+    """The first compiled tile and every rotation tile: the batch builds its
+    tables entry by entry (`direct_table_entry`), the single call with the
+    tables kernel (angles per coordinate, rotation offsets stepped by the
+    first difference), so equal bits also check that the two table builders
+    agree."""
+    tiles = cg.cgh_direct_tiles()
+    return [tiles[0]] + [t for t in tiles if t[7] >= 6]
+
+
 def test_direct_batch_equals_single_calls(cg, h, oracle_mod):
     import torch
     clouds = _small_clouds()
     probs = _problems(clouds)
-    tile = cg.cgh_direct_tiles()[0]
-    cg.cgh_set_direct_tile(h, tile)
+    refs = [oracle_mod.forward(c) if c.N else None for c in clouds]
     # the batch runs whole tiles like the one-CTA-per-tile schedule: the same
     # summation order, so the same bits
     try:
-        cg.cgh_set_direct_schedule(h, "grid")
-        cg.cgh_batch(probs, method="direct", handle=h)
-        torch.cuda.synchronize()
-        assert cg.cgh_last_device_status(h) == cg.CGH_OK
-        for c, pr in zip(clouds, probs):
-            got = pr["out"].cpu().numpy()
-            pts, A, z = to_dev(c)
-            single = cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, handle=h)
-            assert np.array_equal(got, single.cpu().numpy())
-            cg.cgh_set_direct_schedule(h, "split")
-            split = cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, handle=h)
+        for tile in _batch_tiles(cg):
+            cg.cgh_set_direct_tile(h, tile)
             cg.cgh_set_direct_schedule(h, "grid")
-            assert max_abs(got, split.cpu().numpy()) <= 1e-5 * max(sum_abs_A(c), 1.0)
-            if c.N:
-                assert max_abs(got, oracle_mod.forward(c)) <= 1e-4 * sum_abs_A(c)
-            else:
-                assert np.all(got == 0)
+            cg.cgh_batch(probs, method="direct", handle=h)
+            torch.cuda.synchronize()
+            assert cg.cgh_last_device_status(h) == cg.CGH_OK
+            for c, pr, ref in zip(clouds, probs, refs):
+                got = pr["out"].cpu().numpy()
+                pts, A, z = to_dev(c)
+                single = cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, handle=h)
+                assert np.array_equal(got, single.cpu().numpy()), tile
+                cg.cgh_set_direct_schedule(h, "split")
+                split = cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, handle=h)
+                cg.cgh_set_direct_schedule(h, "grid")
+                assert max_abs(got, split.cpu().numpy()) <= 1e-5 * max(sum_abs_A(c), 1.0)
+                if c.N:
+                    assert max_abs(got, ref) <= 1e-4 * sum_abs_A(c), tile
+                else:
+                    assert np.all(got == 0)
     finally:
         cg.cgh_set_direct_schedule(h, "auto")
+        cg.cgh_set_direct_tile(h, None)
 
 
 def test_graph_replay_rereads_inputs(cg, h, oracle_mod):
