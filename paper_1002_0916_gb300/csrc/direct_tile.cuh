@@ -296,7 +296,8 @@ struct DirectTileLoop {
     // PKV: 0 scalar arithmetic, 1 packed FP32x2 with the degree-6 polynomial,
     // 2 packed with the degree-5 polynomial, 3 as 2 with the polynomial pairs
     // interleaved, 4 and 5 as 3 with one extra polynomial pair on every
-    // second (4) or fourth (5) point
+    // second (4) or fourth (5) point; 6-8 the rotation forms (one sincos per
+    // thread row (6) or per thread (7 scalar, 8 packed) and point)
     static constexpr bool PK = PKV != 0;
     static constexpr int NPAIRS = VX * VY / 2;
     // points per period of the polynomial pattern
