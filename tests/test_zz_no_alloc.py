@@ -87,6 +87,34 @@ def test_noalloc_against_the_oracle(cg, oracle_mod):
             assert err <= TOL * sum_abs_A(c), err
 
 
+def test_noalloc_runs_a_rotation_tile(cg, oracle_mod):
+    """A frame whose built-in tile is a rotation tile and whose rotation tables
+    (twice the angle tables) fit the array: 1024 x 1024 with 512 points needs
+    8.4 MB.  The call runs that tile; checked against cgh_forward and the
+    oracle on sampled rows, twice in a row."""
+    import torch
+    c = make_cloud(91, 512, 1024, 1024, integer=False, zlo=0.4, zhi=1.4,
+                   lam=532e-9, p=8e-6)
+    h = cg.cgh_create(0)
+    try:
+        assert cg.cgh_direct_tile_for(h, c.N, c.Nx, c.Ny)[7] >= 6
+        pts, A, z = to_dev(c)
+        ref_gpu = cg.cgh_forward(pts, A, z, c.lam, c.p, c.Nx, c.Ny, method="direct",
+                                 handle=h).cpu().numpy()
+    finally:
+        cg.cgh_destroy(h)
+    rows = sample_rows(c.Ny, 16, seed=5)
+    ref = oracle_mod.forward(c, rows=rows)
+    for _ in range(2):
+        out = torch.full((c.Ny, c.Nx), float("nan"), device="cuda")
+        assert _noalloc(cg, c, out) == cg.CGH_OK
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert max_abs(got, ref_gpu) <= 1e-5 * sum_abs_A(c)
+        assert max_abs(got[rows], ref) <= TOL * sum_abs_A(c)
+
+
 def test_noalloc_empty_cloud_gives_zeros(cg):
     import torch
     e = torch.zeros(0, device="cuda")
