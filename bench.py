@@ -532,6 +532,11 @@ def kernel_roofline(kernel, pp, flops, ms, sms, peaks, pipe_rates=None, sm_mhz=N
                 sms * MUFU_PER_CLK_PER_SM / mufu_per_pp * NOMINAL_MAX_MHZ * 1e6 / 1e9)
         if sm_mhz:
             roof["frac_at_observed_clock"] = achieved / (sms * per_clk * sm_mhz * 1e6 / 1e9)
+        if kernel in ("direct", "batch") and tile and tile[7] >= 6:
+            # the rotation forms against the bound of the cosine-per-pixel
+            # recipe they replace (above 1: faster than that recipe can be)
+            roof["vs_cosine_per_pixel_bound"] = achieved / (
+                sms * MIXED_PP_PER_CLK_PER_SM * NOMINAL_MAX_MHZ * 1e6 / 1e9)
         return roof
     if kernel in GEMM_KERNELS and flops:
         achieved = flops / (ms / 1e3) / 1e12

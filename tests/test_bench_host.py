@@ -80,3 +80,13 @@ def test_rotation_recipes():
     assert bench.alu_recipe("direct")[0] == bench.MIXED_PP_PER_CLK_PER_SM
     assert bench.alu_recipe("direct", (32, 32, 4, 4, 64, 4, 4, 5))[0] == \
         bench.MIXED_PP_PER_CLK_PER_SM
+
+
+def test_rotation_roofline_reports_the_old_bound():
+    tile = (64, 64, 8, 8, 32, 0, 4, 8)
+    r = bench.kernel_roofline("direct", 2.013e9, 0.0, 0.194, 152, {}, tile=tile)
+    old = 152 * bench.MIXED_PP_PER_CLK_PER_SM * bench.NOMINAL_MAX_MHZ * 1e6 / 1e9
+    assert abs(r["vs_cosine_per_pixel_bound"] - r["achieved"] / old) < 1e-12
+    assert r["frac"] < 1.0 < r["vs_cosine_per_pixel_bound"]
+    assert "vs_cosine_per_pixel_bound" not in bench.kernel_roofline(
+        "direct", 2.013e9, 0.0, 0.33, 152, {}, tile=(32, 32, 4, 4, 64, 4, 4, 5))
