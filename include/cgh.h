@@ -310,7 +310,15 @@ typedef struct {
                               polynomial pixel pairs spread over the
                               thread's block; 4, 5: as 3 with
                               poly_pixels + 2 polynomial pixels for
-                              every second (4) or fourth (5) point  */
+                              every second (4) or fourth (5) point;
+                              6-8: the rotation forms (Eq. 1's phase
+                              split into its x and y parts, cos of a
+                              sum): per point, one hardware sincos
+                              per thread row (6) or per thread (7
+                              scalar, 8 packed), every other pixel of
+                              the thread's block by angle addition
+                              with the tabulated cosine and sine of
+                              its exact phase offset (poly_pixels 0) */
 } cgh_direct_tile;
 
 /* How the direct kernel spreads its pixel tiles over the SMs (a scheduling
