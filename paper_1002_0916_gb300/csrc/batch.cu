@@ -394,9 +394,10 @@ cgh_status cgh_ctx::batch(const cgh_problem *probs, int count, int method,
         cgh_status st = check_problem(p.points, p.A, p.z, p.N, p.lambda, p.p, p.Nx,
                                       p.Ny, p.out);
         if (st) {
-            char msg[512];
+            // (the message names the problem; a long one is cut to fit)
+            char msg[sizeof(err) + 32];
             snprintf(msg, sizeof(msg), "problem %d: %s", i, err);
-            snprintf(err, sizeof(err), "%s", msg);
+            snprintf(err, sizeof(err), "%.*s", (int)sizeof(err) - 1, msg);
             return st;
         }
     }
