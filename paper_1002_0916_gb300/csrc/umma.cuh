@@ -142,8 +142,9 @@ __device__ __forceinline__ void tmem_ld_wait() {
 }  // namespace umma
 
 // One problem of a grouped split GEMM: its four tensor maps (A hi, B hi,
-// A lo, B lo) live in global memory, 64-byte aligned, and are read by TMA.
-struct alignas(64) GroupProb {
+// A lo, B lo) live in global memory and are read by TMA, which wants them
+// 64-byte aligned; the struct keeps CUtensorMap's own 128-byte alignment.
+struct alignas(alignof(CUtensorMap)) GroupProb {
     CUtensorMap tA, tB, tA2, tB2;
     float *D;
     long long ldd;
